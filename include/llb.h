@@ -1,0 +1,197 @@
+/*
+ * llb.h -- C ABI of libllb, a GB300 (sm_103a) implementation of the
+ * moment-only ("lightweight", "without populations") lattice Boltzmann
+ * step of Tiribocchi et al., "Lightweight Lattice Boltzmann",
+ * arXiv 2301.01622.
+ *
+ * What one step computes (Sec. II and III A of the paper): every node holds
+ * only its hydrodynamic moments -- density rho, momentum j = rho u and the
+ * momentum-flux tensor P (Eq. HYD), ten fields for one component and eleven
+ * for two.  A step reconstructs each neighbour's post-collision population
+ * from that neighbour's moments (Eq. oper, eq-part, neq-part, coll2),
+ * pull-streams it (Eq. stream, read as h_i(x, t+1) = h'_i[H(x - c_i, t)]),
+ * and sums the streamed populations into the new moments (Eq. HYD).  Two
+ * flip-flop copies of the moment arrays hold times t and t+1 (Sec. III A).
+ * Boundaries are periodic in x, y and z.
+ *
+ * Canonical moment layout (every host or device buffer that crosses this
+ * ABI): field-major, x fastest, element (f, z, y, x) at index
+ * ((f * nz + z) * ny + y) * nx + x, fields in the order
+ *   one component : rho, j_x, j_y, j_z, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz
+ *   two components: rho1, rho2, j_x, j_y, j_z, P_xx, ..., P_yz
+ * The moments are the pre-collision moments at integer time t.
+ *
+ * Ownership: the library owns the context and, unless the caller passes its
+ * own device buffers in llb_params.buffers, the device state.  Host and device
+ * buffers passed to the calls below stay owned by the caller; the library
+ * copies from or into them and never keeps the pointer.
+ *
+ * Errors: every call returns LLB_OK (0) or a negative LLB_E* code; no C++
+ * exception crosses the ABI.  A CUDA error inside a call makes the context
+ * sticky-failed: every later call returns LLB_ESTATE until llb_destroy.
+ * llb_last_error() returns a human-readable message for the last failure.
+ *
+ * Streams: all device work of a context is enqueued on llb_params.stream
+ * (a cudaStream_t; NULL = the legacy default stream).  llb_step is
+ * asynchronous; llb_get_moments, llb_diagnostics and llb_synchronize wait
+ * for the stream.
+ */
+#ifndef LLB_H
+#define LLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LLB_API __attribute__((visibility("default")))
+#else
+#define LLB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LLB_OK         0
+#define LLB_EINVAL    -1  /* bad argument (sizes, tau, lattice, pointer)   */
+#define LLB_ENOMEM    -2  /* device or host allocation failed              */
+#define LLB_ECUDA     -3  /* a CUDA runtime call or kernel launch failed   */
+#define LLB_EUNSTABLE -4  /* non-finite value or rho <= 0 seen             */
+#define LLB_ETIMEOUT  -5  /* a bounded device wait gave up                 */
+#define LLB_ESTATE    -6  /* context unusable after an earlier CUDA error  */
+
+/* ---- element types (storage on the device, and host/device buffers) -- */
+#define LLB_F64 0   /* double                                              */
+#define LLB_F32 1   /* float                                               */
+
+/* ---- schemes --------------------------------------------------------- */
+/* The moment-only scheme of the paper (Sec. II-III A). */
+#define LLB_SCHEME_MOMENT          0
+/* Population-storing regularized LB: stores all Q populations and applies
+ * the same collision (Eq. coll2 on the projected moments) -- the same map as
+ * LLB_SCHEME_MOMENT in exact arithmetic, used as the in-project baseline.  */
+#define LLB_SCHEME_POPULATION      1
+/* Population-storing plain BGK (Eq. coll applied to the stored populations,
+ * ghosts kept): the "standard LB with populations" of Sec. IV.            */
+#define LLB_SCHEME_POPULATION_BGK  2
+
+/* ---- kernel choice for LLB_SCHEME_MOMENT ----------------------------- */
+#define LLB_KERNEL_AUTO   0  /* fastest available for the shape            */
+#define LLB_KERNEL_DIRECT 1  /* one thread per node, gathers Q neighbours  */
+#define LLB_KERNEL_TILED  2  /* z-marching shared-memory tile kernel       */
+
+typedef struct llb_ctx llb_ctx;
+
+typedef struct llb_params {
+    int ncomp;        /* 1 (default) or 2 components                         */
+    int storage;      /* LLB_F32 (default) or LLB_F64                        */
+    int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
+    int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
+    /* two-component colour-gradient / near-contact parameters (Sec. III A-B) */
+    double beta;      /* recolouring strength, default 0.7                   */
+    double A_s;       /* surface-tension (perturbation) strength, default 0.01 */
+    double A_h;       /* near-contact repulsion strength, default 0.0        */
+    double g_min;     /* |grad phi| below which the normal is zero, default 1e-6 */
+    int h_c;          /* near-contact probe range in nodes, default 3        */
+    void* stream;     /* cudaStream_t; NULL = legacy default stream          */
+    /* Optional caller-owned device buffers for the two flip-flop copies of
+     * the state, each at least llb_state_bytes() bytes and 256-byte aligned.
+     * NULL = the library allocates (and frees) them.                       */
+    void* buffers[2];
+} llb_params;
+
+typedef struct llb_diag {
+    double mass[2];     /* sum of rho (one component) or of rho1, rho2     */
+    double momentum[3]; /* sum of j                                        */
+    double rho1_sum;    /* sum of rho (rho1 for two components) over nodes where it is > 0.5 */
+    long long n_in;     /* number of such nodes                            */
+    double rho1_avg;    /* rho1_sum / n_in (0 if n_in == 0): <rho>_{rho>0.5}, Sec. IV Fig. 2 */
+    double min_rho;     /* minimum total density                           */
+    int flags;          /* bit 0: non-finite value seen; bit 1: min_rho <= 0 */
+    int reserved;
+} llb_diag;
+
+#define LLB_FLAG_NONFINITE   1
+#define LLB_FLAG_NONPOSITIVE 2
+
+typedef struct llb_footprint {
+    int arrays;               /* whole-domain arrays held on the device, both flip-flop copies */
+    int fields;               /* arrays per copy (10/11 moments, Q or 2Q populations) */
+    size_t bytes_per_node;    /* state bytes per node, both copies           */
+    size_t state_bytes;       /* bytes of one copy                           */
+    size_t stream_bytes_per_node; /* algorithmic DRAM bytes per node per step (read + write) */
+} llb_footprint;
+
+/* Fill *p with the defaults listed in llb_params.  Never fails. */
+LLB_API void llb_params_default(llb_params* p);
+
+/* Storage accounting without touching a GPU (Sec. III A: 20 vs 38 arrays for
+ * one component on D3Q19, 22 vs 76 for two).  p may be NULL (defaults).
+ * Returns LLB_EINVAL on bad sizes or parameters. */
+LLB_API int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p,
+                        llb_footprint* out);
+
+/* Bytes of one state copy (what each of llb_params.buffers must hold). */
+LLB_API int llb_state_bytes(int nx, int ny, int nz, int lattice, const llb_params* p, size_t* out);
+
+/* Create a context for an nx * ny * nz periodic box on the current CUDA
+ * device.  lattice: 19 (D3Q19) or 27 (D3Q27).  tau: BGK relaxation time,
+ * tau > 1/2 (viscosity nu = cs^2 (tau - 1/2), Sec. III B).  nx, ny, nz >= 1.
+ * Two components need nx, ny, nz >= 4.  p may be NULL (defaults).
+ * The state is zero until one of the llb_init_* calls.  On failure *out is
+ * NULL and nothing is leaked. */
+LLB_API int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau,
+               const llb_params* p);
+
+/* Release everything the context owns.  NULL-safe.  Waits for the stream. */
+LLB_API void llb_destroy(llb_ctx* ctx);
+
+/* Load canonical moments (layout above) from HOST memory of element type
+ * host_dtype (LLB_F64 or LLB_F32).  Copies through a device staging buffer
+ * and converts on the device.  Rejects rho <= 0 or non-finite input with
+ * LLB_EUNSTABLE (checked on the device, the call synchronises).  Resets the
+ * step counter to 0. */
+LLB_API int llb_init_moments(llb_ctx* ctx, const void* host_m, int host_dtype);
+
+/* Same, from DEVICE memory (e.g. a torch tensor), asynchronous, no check. */
+LLB_API int llb_init_moments_device(llb_ctx* ctx, const void* dev_m, int dtype);
+
+/* Initialise at local equilibrium, P = cs^2 rho I + rho u u (the second
+ * moment of Eq. eq-part), from HOST arrays: rho (ncomp fields: rho, or
+ * rho1 then rho2) and u (3 fields), canonical layout, element type
+ * host_dtype. */
+LLB_API int llb_init_equilibrium(llb_ctx* ctx, const void* host_rho, const void* host_u, int host_dtype);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the context stream). */
+LLB_API int llb_step(llb_ctx* ctx, int nsteps);
+
+/* Copy the current canonical moments into caller HOST memory of element
+ * type host_dtype.  Synchronises the stream. */
+LLB_API int llb_get_moments(llb_ctx* ctx, void* host_out, int host_dtype);
+
+/* Same into caller DEVICE memory, asynchronous. */
+LLB_API int llb_get_moments_device(llb_ctx* ctx, void* dev_out, int dtype);
+
+/* FP64 reductions of the current state (Sec. IV, Figs. 2, 5, 7 and mass /
+ * momentum conservation).  Synchronises the stream. */
+LLB_API int llb_diagnostics(llb_ctx* ctx, llb_diag* out);
+
+/* Wait for all work of the context. */
+LLB_API int llb_synchronize(llb_ctx* ctx);
+
+/* Steps taken since the last llb_init_*. */
+LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
+
+/* Device pointer of the current state copy, its element type and the kernel
+ * the context runs (for profiling and zero-copy views). */
+LLB_API int llb_state_device(const llb_ctx* ctx, void** dev_ptr, int* dtype, int* kernel);
+
+/* Static strings; never NULL. */
+LLB_API const char* llb_status_string(int status);
+LLB_API const char* llb_last_error(const llb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LLB_H */

@@ -1,0 +1,397 @@
+// extern "C" entry points of libllb: argument checking, device memory,
+// host <-> device transfers and dispatch to the kernels.  Every step of the
+// lattice Boltzmann update runs in the CUDA kernels of this library; the
+// host code only validates, allocates, copies and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace llb {
+
+size_t elem_size(int dtype) { return dtype == LLB_F64 ? 8 : dtype == LLB_F32 ? 4 : 0; }
+
+int canonical_fields(const llb_ctx& c) { return c.ncomp == 2 ? 11 : 10; }
+
+int fields_of(const llb_ctx& c) {
+    if (c.scheme == LLB_SCHEME_MOMENT) return canonical_fields(c);
+    return c.Q * c.ncomp;
+}
+
+}  // namespace llb
+
+using namespace llb;
+
+namespace {
+
+int fail(llb_ctx* c, int code, const std::string& m) {
+    if (c) {
+        c->msg = m;
+        if (code == LLB_ECUDA) c->sticky = LLB_ECUDA;
+    }
+    return code;
+}
+
+int cuda_fail(llb_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, LLB_ECUDA, m);
+}
+
+#define LLB_CHECK_CTX(c)                         \
+    do {                                         \
+        if (!(c)) return LLB_EINVAL;             \
+        if ((c)->sticky != LLB_OK) return LLB_ESTATE; \
+    } while (0)
+
+#define LLB_CUDA(c, expr, where)                              \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, where); \
+    } while (0)
+
+bool dtype_ok(int dt) { return dt == LLB_F64 || dt == LLB_F32; }
+
+// Validate shape and parameters; fill the shape-only fields of *c.
+int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& p, llb_ctx* c, std::string* why) {
+    if (nx < 1 || ny < 1 || nz < 1) { *why = "nx, ny, nz must be >= 1"; return LLB_EINVAL; }
+    if (lattice != 19 && lattice != 27) { *why = "lattice must be 19 or 27"; return LLB_EINVAL; }
+    if (!(tau > 0.5) || !std::isfinite(tau)) { *why = "tau must be finite and > 1/2 (nu = cs^2 (tau - 1/2) > 0)"; return LLB_EINVAL; }
+    if (p.ncomp != 1 && p.ncomp != 2) { *why = "ncomp must be 1 or 2"; return LLB_EINVAL; }
+    if (!dtype_ok(p.storage)) { *why = "storage must be LLB_F32 or LLB_F64"; return LLB_EINVAL; }
+    if (p.scheme != LLB_SCHEME_MOMENT && p.scheme != LLB_SCHEME_POPULATION && p.scheme != LLB_SCHEME_POPULATION_BGK) {
+        *why = "unknown scheme"; return LLB_EINVAL;
+    }
+    if (p.kernel != LLB_KERNEL_AUTO && p.kernel != LLB_KERNEL_DIRECT && p.kernel != LLB_KERNEL_TILED) {
+        *why = "unknown kernel"; return LLB_EINVAL;
+    }
+    if (p.ncomp == 2) {
+        *why = "two-component model not available in this build";
+        return LLB_EINVAL;
+    }
+    const double n = (double)nx * ny * nz;
+    if (n > 4.0e9) { *why = "domain too large"; return LLB_EINVAL; }
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->Q = lattice;
+    c->tau = tau;
+    c->omega = 1.0 / tau;
+    c->ncomp = p.ncomp;
+    c->storage = p.storage;
+    c->scheme = p.scheme;
+    c->kernel = p.kernel;
+    c->params = p;
+    c->N = (size_t)nx * ny * nz;
+    c->nf = fields_of(*c);
+    c->elem = elem_size(p.storage);
+    return LLB_OK;
+}
+
+int ensure_staging(llb_ctx* c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return LLB_OK;
+    if (c->staging) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->staging);
+        c->staging = nullptr;
+        c->staging_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->staging, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LLB_ENOMEM, "cudaMalloc of the staging buffer failed");
+    }
+    c->staging_bytes = bytes;
+    return LLB_OK;
+}
+
+// Shifted moments of the current state: the state itself (moment scheme), or
+// the projection of the pulled populations into the spare flip-flop copy.
+int current_moments(llb_ctx* c, const void** mom) {
+    if (c->scheme == LLB_SCHEME_MOMENT) {
+        *mom = c->buf[c->cur];
+        return LLB_OK;
+    }
+    void* tmp = c->buf[1 - c->cur];
+    LLB_CUDA(c, launch_moments_from_population(*c, c->buf[c->cur], tmp), "project populations");
+    *mom = tmp;
+    return LLB_OK;
+}
+
+// After shifted moments were written to `mom`, build the state from them.
+int finish_init(llb_ctx* c, void* mom) {
+    if (c->scheme != LLB_SCHEME_MOMENT)
+        LLB_CUDA(c, launch_population_from_moments(*c, mom, c->buf[c->cur]), "reconstruct populations");
+    c->t = 0;
+    return LLB_OK;
+}
+
+// Where the init kernels write shifted moments before finish_init.
+void* init_target(llb_ctx* c) {
+    return c->scheme == LLB_SCHEME_MOMENT ? c->buf[c->cur] : c->buf[1 - c->cur];
+}
+
+int check_bad_flag(llb_ctx* c) {
+    int bad = 0;
+    LLB_CUDA(c, cudaMemcpyAsync(&bad, c->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag copy");
+    LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
+    if (bad) return fail(c, LLB_EUNSTABLE, "input has rho <= 0 or a non-finite value");
+    return LLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void llb_params_default(llb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->ncomp = 1;
+    p->storage = LLB_F32;
+    p->scheme = LLB_SCHEME_MOMENT;
+    p->kernel = LLB_KERNEL_AUTO;
+    p->beta = 0.7;
+    p->A_s = 0.01;
+    p->A_h = 0.0;
+    p->g_min = 1e-6;
+    p->h_c = 3;
+    p->stream = nullptr;
+    p->buffers[0] = p->buffers[1] = nullptr;
+}
+
+int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p, llb_footprint* out) {
+    if (!out) return LLB_EINVAL;
+    llb_params d;
+    llb_params_default(&d);
+    llb_ctx c;
+    std::string why;
+    llb_params q = p ? *p : d;
+    // the accounting does not depend on whether the two-component kernels are built
+    const int ncomp = q.ncomp;
+    if (ncomp == 2) q.ncomp = 1;
+    int rc = validate(nx, ny, nz, lattice, 0.75, q, &c, &why);
+    if (rc != LLB_OK) return rc;
+    if (ncomp != 1 && ncomp != 2) return LLB_EINVAL;
+    c.ncomp = ncomp;
+    c.nf = fields_of(c);
+    out->fields = c.nf;
+    out->arrays = 2 * c.nf;
+    out->bytes_per_node = 2 * (size_t)c.nf * c.elem;
+    out->state_bytes = (size_t)c.nf * c.elem * c.N;
+    out->stream_bytes_per_node = 2 * (size_t)c.nf * c.elem;
+    return LLB_OK;
+}
+
+int llb_state_bytes(int nx, int ny, int nz, int lattice, const llb_params* p, size_t* out) {
+    if (!out) return LLB_EINVAL;
+    llb_footprint f;
+    int rc = llb_footprint_query(nx, ny, nz, lattice, p, &f);
+    if (rc == LLB_OK) *out = f.state_bytes;
+    return rc;
+}
+
+int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, const llb_params* p) {
+    if (!out) return LLB_EINVAL;
+    *out = nullptr;
+    llb_params d;
+    llb_params_default(&d);
+    const llb_params& prm = p ? *p : d;
+    llb_ctx* c = new (std::nothrow) llb_ctx();
+    if (!c) return LLB_ENOMEM;
+    std::string why;
+    int rc = validate(nx, ny, nz, lattice, tau, prm, c, &why);
+    if (rc != LLB_OK) {
+        delete c;
+        return rc;
+    }
+    c->stream = static_cast<cudaStream_t>(prm.stream);
+    auto bail = [&](int code) {
+        llb_destroy(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LLB_ECUDA);
+    }
+    const size_t bytes = (size_t)c->nf * c->elem * c->N;
+    for (int b = 0; b < 2; ++b) {
+        if (prm.buffers[b]) {
+            if (reinterpret_cast<uintptr_t>(prm.buffers[b]) % 256 != 0) return bail(LLB_EINVAL);
+            c->buf[b] = prm.buffers[b];
+            c->owns[b] = false;
+        } else {
+            if (cudaMalloc(&c->buf[b], bytes) != cudaSuccess) { cudaGetLastError(); c->buf[b] = nullptr; return bail(LLB_ENOMEM); }
+            c->owns[b] = true;
+        }
+        if (cudaMemsetAsync(c->buf[b], 0, bytes, c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
+    }
+    c->diag_scratch_bytes = (size_t)diag_blocks(*c) * 8 * sizeof(double) + 256;
+    if (cudaMalloc(&c->diag_scratch, c->diag_scratch_bytes + sizeof(llb_diag)) != cudaSuccess) { cudaGetLastError(); c->diag_scratch = nullptr; return bail(LLB_ENOMEM); }
+    if (cudaMalloc(&c->flag_dev, sizeof(int)) != cudaSuccess) { cudaGetLastError(); c->flag_dev = nullptr; return bail(LLB_ENOMEM); }
+    if (c->scheme == LLB_SCHEME_MOMENT) {
+        if (c->kernel == LLB_KERNEL_AUTO || c->kernel == LLB_KERNEL_TILED) {
+            c->tile_ctas = moment_tiled_ctas(*c);
+            cudaGetLastError();
+            if (c->tile_ctas > 0) c->kernel = LLB_KERNEL_TILED;
+            else if (c->kernel == LLB_KERNEL_TILED) return bail(LLB_EINVAL);
+            else c->kernel = LLB_KERNEL_DIRECT;
+        }
+    } else {
+        c->kernel = LLB_KERNEL_DIRECT;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
+    *out = c;
+    return LLB_OK;
+}
+
+void llb_destroy(llb_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int b = 0; b < 2; ++b)
+        if (c->owns[b] && c->buf[b]) cudaFree(c->buf[b]);
+    if (c->staging) cudaFree(c->staging);
+    if (c->diag_scratch) cudaFree(c->diag_scratch);
+    if (c->flag_dev) cudaFree(c->flag_dev);
+    cudaGetLastError();
+    delete c;
+}
+
+int llb_init_moments(llb_ctx* c, const void* host_m, int host_dtype) {
+    LLB_CHECK_CTX(c);
+    if (!host_m || !dtype_ok(host_dtype)) return fail(c, LLB_EINVAL, "null buffer or bad dtype");
+    const size_t bytes = (size_t)canonical_fields(*c) * c->N * elem_size(host_dtype);
+    int rc = ensure_staging(c, bytes);
+    if (rc != LLB_OK) return rc;
+    LLB_CUDA(c, cudaMemsetAsync(c->flag_dev, 0, sizeof(int), c->stream), "flag reset");
+    LLB_CUDA(c, cudaMemcpyAsync(c->staging, host_m, bytes, cudaMemcpyHostToDevice, c->stream), "H2D moments");
+    void* mom = init_target(c);
+    LLB_CUDA(c, launch_canonical_to_shifted(*c, c->staging, host_dtype, mom, static_cast<int*>(c->flag_dev)), "convert");
+    rc = finish_init(c, mom);
+    if (rc != LLB_OK) return rc;
+    return check_bad_flag(c);
+}
+
+int llb_init_moments_device(llb_ctx* c, const void* dev_m, int dtype) {
+    LLB_CHECK_CTX(c);
+    if (!dev_m || !dtype_ok(dtype)) return fail(c, LLB_EINVAL, "null buffer or bad dtype");
+    void* mom = init_target(c);
+    LLB_CUDA(c, launch_canonical_to_shifted(*c, dev_m, dtype, mom, nullptr), "convert");
+    return finish_init(c, mom);
+}
+
+int llb_init_equilibrium(llb_ctx* c, const void* host_rho, const void* host_u, int host_dtype) {
+    LLB_CHECK_CTX(c);
+    if (!host_rho || !host_u || !dtype_ok(host_dtype)) return fail(c, LLB_EINVAL, "null buffer or bad dtype");
+    const size_t es = elem_size(host_dtype);
+    const size_t rho_bytes = (size_t)c->ncomp * c->N * es, u_bytes = 3 * c->N * es;
+    int rc = ensure_staging(c, rho_bytes + u_bytes);
+    if (rc != LLB_OK) return rc;
+    char* st = static_cast<char*>(c->staging);
+    LLB_CUDA(c, cudaMemsetAsync(c->flag_dev, 0, sizeof(int), c->stream), "flag reset");
+    LLB_CUDA(c, cudaMemcpyAsync(st, host_rho, rho_bytes, cudaMemcpyHostToDevice, c->stream), "H2D rho");
+    LLB_CUDA(c, cudaMemcpyAsync(st + rho_bytes, host_u, u_bytes, cudaMemcpyHostToDevice, c->stream), "H2D u");
+    void* mom = init_target(c);
+    LLB_CUDA(c, launch_equilibrium(*c, st, st + rho_bytes, host_dtype, mom, static_cast<int*>(c->flag_dev)), "equilibrium");
+    rc = finish_init(c, mom);
+    if (rc != LLB_OK) return rc;
+    return check_bad_flag(c);
+}
+
+int llb_step(llb_ctx* c, int nsteps) {
+    LLB_CHECK_CTX(c);
+    if (nsteps < 0) return fail(c, LLB_EINVAL, "nsteps must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        const void* in = c->buf[c->cur];
+        void* out = c->buf[1 - c->cur];
+        cudaError_t e;
+        if (c->scheme == LLB_SCHEME_MOMENT)
+            e = c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out) : launch_moment_direct(*c, in, out);
+        else
+            e = launch_population_step(*c, in, out, c->scheme == LLB_SCHEME_POPULATION_BGK);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+        c->cur = 1 - c->cur;
+        ++c->t;
+    }
+    return LLB_OK;
+}
+
+int llb_get_moments(llb_ctx* c, void* host_out, int host_dtype) {
+    LLB_CHECK_CTX(c);
+    if (!host_out || !dtype_ok(host_dtype)) return fail(c, LLB_EINVAL, "null buffer or bad dtype");
+    const size_t bytes = (size_t)canonical_fields(*c) * c->N * elem_size(host_dtype);
+    int rc = ensure_staging(c, bytes);
+    if (rc != LLB_OK) return rc;
+    const void* mom = nullptr;
+    rc = current_moments(c, &mom);
+    if (rc != LLB_OK) return rc;
+    LLB_CUDA(c, launch_shifted_to_canonical(*c, mom, c->staging, host_dtype), "convert");
+    LLB_CUDA(c, cudaMemcpyAsync(host_out, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H moments");
+    LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
+    return LLB_OK;
+}
+
+int llb_get_moments_device(llb_ctx* c, void* dev_out, int dtype) {
+    LLB_CHECK_CTX(c);
+    if (!dev_out || !dtype_ok(dtype)) return fail(c, LLB_EINVAL, "null buffer or bad dtype");
+    const void* mom = nullptr;
+    int rc = current_moments(c, &mom);
+    if (rc != LLB_OK) return rc;
+    LLB_CUDA(c, launch_shifted_to_canonical(*c, mom, dev_out, dtype), "convert");
+    return LLB_OK;
+}
+
+int llb_diagnostics(llb_ctx* c, llb_diag* out) {
+    LLB_CHECK_CTX(c);
+    if (!out) return fail(c, LLB_EINVAL, "null output");
+    const void* mom = nullptr;
+    int rc = current_moments(c, &mom);
+    if (rc != LLB_OK) return rc;
+    llb_diag* dev_out = reinterpret_cast<llb_diag*>(static_cast<char*>(c->diag_scratch) + c->diag_scratch_bytes);
+    LLB_CUDA(c, launch_diagnostics(*c, mom, c->diag_scratch, dev_out), "diagnostics");
+    LLB_CUDA(c, cudaMemcpyAsync(out, dev_out, sizeof(llb_diag), cudaMemcpyDeviceToHost, c->stream), "D2H diag");
+    LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
+    return LLB_OK;
+}
+
+int llb_synchronize(llb_ctx* c) {
+    LLB_CHECK_CTX(c);
+    LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
+    return LLB_OK;
+}
+
+int llb_steps_done(const llb_ctx* c, long long* out) {
+    if (!c || !out) return LLB_EINVAL;
+    *out = c->t;
+    return LLB_OK;
+}
+
+int llb_state_device(const llb_ctx* c, void** dev_ptr, int* dtype, int* kernel) {
+    if (!c) return LLB_EINVAL;
+    if (dev_ptr) *dev_ptr = c->buf[c->cur];
+    if (dtype) *dtype = c->storage;
+    if (kernel) *kernel = c->kernel;
+    return LLB_OK;
+}
+
+const char* llb_status_string(int s) {
+    switch (s) {
+        case LLB_OK: return "ok";
+        case LLB_EINVAL: return "invalid argument";
+        case LLB_ENOMEM: return "out of memory";
+        case LLB_ECUDA: return "CUDA error";
+        case LLB_EUNSTABLE: return "unstable state (rho <= 0 or non-finite)";
+        case LLB_ETIMEOUT: return "device wait timed out";
+        case LLB_ESTATE: return "context unusable after an earlier CUDA error";
+        default: return "unknown status";
+    }
+}
+
+const char* llb_last_error(const llb_ctx* c) {
+    if (!c) return "no context";
+    return c->msg.c_str();
+}
+
+}  // extern "C"

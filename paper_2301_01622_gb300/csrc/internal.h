@@ -1,0 +1,72 @@
+// Internal context and launcher declarations of libllb (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/llb.h"
+
+struct llb_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    int Q = 19;              // 19 or 27
+    int ncomp = 1;
+    int storage = LLB_F32;   // element type of the device state
+    int scheme = LLB_SCHEME_MOMENT;
+    int kernel = LLB_KERNEL_AUTO;  // resolved kernel (never AUTO after create)
+    double tau = 1.0, omega = 1.0;
+    llb_params params{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    size_t N = 0;            // nodes
+    int nf = 0;              // arrays per state copy
+    size_t elem = 4;         // bytes per element of the state
+    void* buf[2] = {nullptr, nullptr};
+    bool owns[2] = {false, false};
+    int cur = 0;             // buf[cur] holds the state at time t
+    void* staging = nullptr; // canonical moments (FP64 worst case) for host/device conversion
+    size_t staging_bytes = 0;
+    void* diag_scratch = nullptr;  // per-block partial sums of the diagnostics
+    size_t diag_scratch_bytes = 0;
+    void* diag_moments = nullptr;  // moments of a population state, for diagnostics
+    void* flag_dev = nullptr;      // device int for init-time checks
+    long long t = 0;
+    int sticky = LLB_OK;
+    std::string msg;
+    // tiled-kernel launch plan
+    int tile_ctas = 0;
+};
+
+namespace llb {
+
+size_t elem_size(int dtype);
+int fields_of(const llb_ctx& c);           // arrays per state copy
+int canonical_fields(const llb_ctx& c);    // 10 or 11
+
+// Moment-only, one component (moment_step.cu)
+cudaError_t launch_moment_direct(const llb_ctx& c, const void* in, void* out);
+cudaError_t launch_moment_tiled(const llb_ctx& c, const void* in, void* out);
+int moment_tiled_ctas(const llb_ctx& c);   // persistent grid size, 0 if the kernel cannot run
+
+// Population-storing baselines (population_step.cu)
+cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);
+// state <- populations reconstructed from shifted moments (un-streamed so a pull reads them)
+cudaError_t launch_population_from_moments(const llb_ctx& c, const void* mom, void* state);
+// shifted moments <- projection of the pulled populations
+cudaError_t launch_moments_from_population(const llb_ctx& c, const void* state, void* mom);
+
+// Conversions between canonical and shifted storage (convert.cu)
+cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int canon_dtype, void* state,
+                                        int* bad_flag);
+cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* state, void* canon, int canon_dtype);
+cudaError_t launch_equilibrium(const llb_ctx& c, const void* rho, const void* u, int dtype, void* state,
+                               int* bad_flag);
+
+// Diagnostics (diagnostics.cu).  `mom` holds shifted moments of type c.storage.
+int diag_blocks(const llb_ctx& c);
+cudaError_t launch_diagnostics(const llb_ctx& c, const void* mom, void* scratch, llb_diag* dev_out);
+
+}  // namespace llb

@@ -1,0 +1,245 @@
+"""GPU parity of the moment-only step (one component) against the FP64 oracle.
+
+Tolerances: FP64 storage 1e-12 relative, FP32 storage 1e-5 relative after
+200 steps, measured per moment group (rho; j; P) as
+max |gpu - oracle| / max |oracle| over the group's fields.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import D3Q19, D3Q27, lb
+from oracle import diagnostics as odg
+from paper_2301_01622_gb300 import inputs, llb
+
+from gpu_helpers import assert_groups, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+LAT = {19: D3Q19, 27: D3Q27}
+KERNELS = [llb.LLB_KERNEL_TILED, llb.LLB_KERNEL_DIRECT]
+KIDS = ["tiled", "direct"]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_tg(q, n, tau, steps, noise):
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=noise, seed=2301)
+    return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], tau, steps)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("kernel", KERNELS, ids=KIDS)
+def test_taylor_green_fp64_200_steps(q, kernel):
+    """32^3 Taylor-Green, u0 = 0.05, tau = 0.8, FP64, 200 steps: 1e-12."""
+    n, tau = 32, 0.8
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05)
+    got, used = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F64, kernel=kernel)
+    assert used == kernel
+    assert_groups(got, oracle_tg(q, n, tau, 200, 0.0), 1e-12, what=f"D3Q{q} fp64")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("kernel", KERNELS, ids=KIDS)
+def test_taylor_green_fp32_200_steps(q, kernel):
+    """Same run with FP32 storage and arithmetic: 1e-5 after 200 steps."""
+    n, tau = 32, 0.8
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05)
+    got, _ = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F32, kernel=kernel)
+    assert_groups(got, oracle_tg(q, n, tau, 200, 0.0), 1e-5, what=f"D3Q{q} fp32")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_noisy_taylor_green_fp32_tau06(q):
+    """The bench workload's field (Taylor-Green + 1e-3 noise, tau = 0.6) on 32^3, FP32, 200 steps."""
+    n, tau = 32, 0.6
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=2301)
+    got, _ = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F32)
+    assert_groups(got, oracle_tg(q, n, tau, 200, 1e-3), 1e-5, what=f"D3Q{q} fp32 noisy")
+
+
+SHAPES = [(67, 45, 37), (33, 9, 5), (31, 17, 3), (5, 70, 2), (1, 1, 1), (2, 3, 4), (4, 4, 4), (64, 16, 8), (97, 1, 3)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("kernel", KERNELS, ids=KIDS)
+def test_ragged_shapes_random_moments_fp64(shape, q, kernel):
+    """Random non-equilibrium moments, shapes spanning several tiles, ragged
+    tails and degenerate 1- and 2-node axes: 1e-12 after 3 steps."""
+    nx, ny, nz = shape
+    m0 = inputs.random_moments(nx, ny, nz, seed=nx * 10007 + ny * 101 + nz)
+    ref = lb.run_moment_only(m0, LAT[q], 0.7, 3)
+    got, _ = run_gpu(shape, q, 0.7, 3, m0=m0, storage=llb.LLB_F64, kernel=kernel)
+    assert_groups(got, ref, 1e-12, what=f"{shape} D3Q{q}")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_zero_steps_round_trip(q):
+    m0 = inputs.random_moments(7, 5, 3, seed=3)
+    got, _ = run_gpu((7, 5, 3), q, 0.9, 0, m0=m0, storage=llb.LLB_F64)
+    np.testing.assert_allclose(got, m0, rtol=0, atol=2e-16)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_tiled_is_deterministic_and_matches_direct(q):
+    n = 40
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=5)
+    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
+    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
+    c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
+    assert np.array_equal(a, b)
+    assert_groups(a, c, 1e-6, what="tiled vs direct")
+
+
+def _sample_nodes(nx, ny, nz, rng, count=60):
+    pts = set()
+    for x in (0, 1, 30, 31, 32, 33, nx - 1):
+        for y in (0, 7, 8, ny - 1):
+            for z in (0, nz // 2, nz - 1):
+                pts.add((x % nx, y % ny, z % nz))
+    for _ in range(count):
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))))
+    return sorted(pts)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_full_size_256_sampled_nodes(q):
+    """The bench configuration (256^3, Taylor-Green + 1e-3 noise, tau = 0.6,
+    FP32, the kernel bench.py times): one step, sampled nodes against the
+    oracle's per-node evaluation of the same initial field."""
+    n, tau = 256, 0.6
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=2301)
+    m0 = lb.equilibrium_moments(rho, u)
+    got, used = run_gpu((n, n, n), q, tau, 1, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_AUTO)
+    assert used == llb.LLB_KERNEL_TILED
+    rng = np.random.default_rng(q)
+    pts = _sample_nodes(n, n, n, rng)
+    ref = np.stack([lb.node_moment_only(m0, LAT[q], tau, x, y, z) for (x, y, z) in pts], axis=1)
+    gs = np.stack([got[:, z, y, x] for (x, y, z) in pts], axis=1)
+    assert_groups(gs[:, :, None, None], ref[:, :, None, None], 1e-6, what="256^3 sampled")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_full_size_conservation(q):
+    """Mass and momentum over 50 steps of the 256^3 FP32 bench workload (FP64 reductions)."""
+    n, tau = 256, 0.6
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=2301)
+    p = llb.llb_params_default(storage=llb.LLB_F32)
+    ctx = llb.llb_create(n, n, n, q, tau, p)
+    try:
+        llb.llb_init_equilibrium(ctx, rho, u)
+        d0 = llb.llb_diagnostics(ctx)
+        llb.llb_step(ctx, 50)
+        d1 = llb.llb_diagnostics(ctx)
+    finally:
+        llb.llb_destroy(ctx)
+    N = n ** 3
+    assert abs(d1["mass"][0] - d0["mass"][0]) <= 1e-12 * N
+    for a in range(3):
+        assert abs(d1["momentum"][a] - d0["momentum"][a]) <= 1e-9 * N
+    assert d1["flags"] == 0 and d1["min_rho"] > 0.9
+
+
+@pytest.mark.parametrize("storage", [llb.LLB_F64, llb.LLB_F32])
+def test_diagnostics_match_oracle(storage):
+    """llb_diagnostics vs the oracle's FP64 diagnostics on the same field."""
+    nx, ny, nz = 45, 33, 17
+    m0 = inputs.random_moments(nx, ny, nz, seed=17, rho_spread=0.6)
+    if storage == llb.LLB_F32:
+        # the device stores d = rho - 1 in FP32; give the oracle the same values
+        d32 = (m0[0] - 1.0).astype(np.float32).astype(np.float64)
+        m0 = m0.copy()
+        m0[0] = 1.0 + d32
+        m0[1:4] = m0[1:4].astype(np.float32).astype(np.float64)
+    p = llb.llb_params_default(storage=storage)
+    ctx = llb.llb_create(nx, ny, nz, 19, 0.8, p)
+    try:
+        llb.llb_init_moments(ctx, m0)
+        d = llb.llb_diagnostics(ctx)
+    finally:
+        llb.llb_destroy(ctx)
+    ref = odg.diagnostics(m0, ncomp=1)
+    assert d["n_in"] == ref["n_in"]
+    assert abs(d["mass"][0] - ref["mass"][0]) <= 1e-12 * abs(ref["mass"][0])
+    for a in range(3):
+        assert abs(d["momentum"][a] - ref["momentum"][a]) <= 1e-12 * nx * ny * nz
+    assert abs(d["rho1_avg"] - ref["rho1_avg"]) <= 1e-13
+    assert abs(d["min_rho"] - ref["min_rho"]) <= 1e-15
+    assert d["flags"] == 0
+
+
+def test_init_rejects_unphysical_input():
+    """rho <= 0 or NaN in the input is reported as LLB_EUNSTABLE (checked on the device)."""
+    m0 = inputs.random_moments(8, 8, 8, seed=2)
+    bad = m0.copy()
+    bad[0, 3, 3, 3] = -0.5
+    nan = m0.copy()
+    nan[6, 1, 2, 3] = np.nan
+    ctx = llb.llb_create(8, 8, 8, 19, 0.8, llb.llb_params_default())
+    try:
+        for b in (bad, nan):
+            with pytest.raises(llb.LLBError) as e:
+                llb.llb_init_moments(ctx, b)
+            assert e.value.status == llb.LLB_EUNSTABLE
+        llb.llb_init_moments(ctx, m0)  # the context is still usable
+        llb.llb_step(ctx, 2)
+        assert llb.llb_steps_done(ctx) == 2
+    finally:
+        llb.llb_destroy(ctx)
+
+
+def test_diagnostics_flag_nonfinite_state():
+    """A non-finite value in the state (loaded through the unchecked device
+    path) is flagged by the diagnostics, and propagates through a step."""
+    torch = pytest.importorskip("torch")
+    m0 = inputs.random_moments(16, 16, 16, seed=4)
+    m0[5, 2, 3, 4] = np.inf
+    ctx = llb.llb_create(16, 16, 16, 19, 0.8, llb.llb_params_default(storage=llb.LLB_F64))
+    try:
+        dev = torch.from_numpy(m0).cuda()
+        torch.cuda.synchronize()
+        llb.llb_init_moments_device(ctx, dev)
+        d0 = llb.llb_diagnostics(ctx)
+        llb.llb_step(ctx, 1)
+        d1 = llb.llb_diagnostics(ctx)
+    finally:
+        llb.llb_destroy(ctx)
+    assert d0["flags"] & llb.LLB_FLAG_NONFINITE
+    assert d1["flags"] & llb.LLB_FLAG_NONFINITE
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_checkpoint_restart(q):
+    """A checkpoint is the moment field: stopping, saving in FP64 and
+    restarting reproduces a continuous FP64 run to round-off."""
+    n, tau = 24, 0.7
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=8)
+    full, _ = run_gpu((n, n, n), q, tau, 30, rho=rho, u=u, storage=llb.LLB_F64)
+    half, _ = run_gpu((n, n, n), q, tau, 15, rho=rho, u=u, storage=llb.LLB_F64)
+    rest, _ = run_gpu((n, n, n), q, tau, 15, m0=half, storage=llb.LLB_F64)
+    assert_groups(rest, full, 1e-14, what="restart")
+
+
+def test_device_buffers_and_stream_from_torch():
+    """Caller-owned device buffers and a caller stream (torch), device-side init/get."""
+    torch = pytest.importorskip("torch")
+    n, q, tau = 20, 19, 0.8
+    m0 = inputs.random_moments(n, n, n, seed=12)
+    nbytes = llb.llb_state_bytes(n, n, n, q, llb.llb_params_default(storage=llb.LLB_F64))
+    bufs = [torch.empty(nbytes // 8, dtype=torch.float64, device="cuda") for _ in range(2)]
+    s = torch.cuda.Stream()
+    p = llb.llb_params_default(storage=llb.LLB_F64, buffers=bufs, stream=s.cuda_stream)
+    ctx = llb.llb_create(n, n, n, q, tau, p)
+    try:
+        dev_in = torch.from_numpy(m0).cuda()
+        torch.cuda.synchronize()
+        llb.llb_init_moments_device(ctx, dev_in)
+        llb.llb_step(ctx, 4)
+        dev_out = torch.empty_like(dev_in)
+        llb.llb_get_moments_device(ctx, dev_out)
+        llb.llb_synchronize(ctx)
+        got = dev_out.cpu().numpy()
+    finally:
+        llb.llb_destroy(ctx)
+    assert_groups(got, lb.run_moment_only(m0, D3Q19, tau, 4), 1e-12, what="device buffers")
