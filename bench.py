@@ -1,0 +1,437 @@
+"""Throughput of the moment-only lattice Boltzmann step on GB300.
+
+Workload (one step = one full time step of the hot path over the box):
+256^3 periodic box, D3Q19, FP32 moments, 3D Taylor-Green vortex u0 = 0.05
+plus seeded U(-1e-3, 1e-3) velocity noise, tau = 0.6.  Metric: MLUPS =
+nodes / (1e6 * seconds per step) (Sec. III C, Eq. mlups), with the HBM
+roofline fraction of the step kernel, and the population-storing LB of the
+same library on the same box and GPU beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (weak scaling; the step has no
+data exchange between replicas).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM peak: moment-only vs stored-population LB, 1 GB300, at oracle tol"
+NX = NY = NZ = 256
+LATTICE = 19
+TAU = 0.6
+U0, NOISE, SEED = 0.05, 1e-3, 2301
+WORKLOAD = "256^3 periodic D3Q19 moment-only LB, FP32, Taylor-Green u0=0.05 + U(-1e-3,1e-3) noise, tau=0.6"
+L2_NOTE = "inputs larger than L2 (each FP32 state copy 671 MB vs 129 MB L2); no flush"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the D3Q27 and population lines")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+
+def dist_setup(ngpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_available() else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _cuda_available():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a float over ranks (the slowest replica defines the job time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks / profiles
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("moment_step.cu", "lattice.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2301_01622_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(key)
+    if not d or d.get("source_sha") != kernel_source_sha():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------------------- GPU timing
+
+
+def make_ctx(llb, lattice, scheme, stream, storage=None):
+    p = llb.llb_params_default(storage=llb.LLB_F32 if storage is None else storage, scheme=scheme,
+                               stream=stream)
+    return llb.llb_create(NX, NY, NZ, lattice, TAU, p)
+
+
+def time_steps(llb, ctx, steps, warmup, world, sampler=None):
+    """Device time of `steps` single-step launches (CUDA events on the context stream)."""
+    import torch
+    llb.llb_step(ctx, warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        llb.llb_step(ctx, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    return ms, clocks
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+
+    from paper_2301_01622_gb300 import inputs, llb
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    rho, u = inputs.taylor_green_3d(NX, NY, NZ, u0=U0, noise=NOISE, seed=SEED)
+    nodes = NX * NY * NZ
+    peak, peak_src = measured_peaks()
+
+    def run(lattice, scheme, sampler=None):
+        ctx = make_ctx(llb, lattice, scheme, stream)
+        try:
+            llb.llb_init_equilibrium(ctx, rho, u)
+            kernel = llb.llb_state_device(ctx)[2]
+            ms, clocks = time_steps(llb, ctx, args.steps, args.warmup, world, sampler)
+            fp = llb.llb_footprint_query(NX, NY, NZ, lattice,
+                                         llb.llb_params_default(scheme=scheme))
+        finally:
+            llb.llb_destroy(ctx)
+        ms_max = reduce_max(ms, world)
+        t_step = ms_max / 1e3 / args.steps
+        mlups = world * nodes / t_step / 1e6
+        gbs = fp.stream_bytes_per_node * nodes / (ms / 1e3 / args.steps) / 1e9
+        return {"mlups": mlups, "ms_per_step": ms_max / args.steps, "achieved_gbs": gbs, "frac": gbs / peak,
+                "bytes_per_node": fp.stream_bytes_per_node, "kernel": kernel, "clocks": clocks,
+                "launch_ms": ms / args.steps}
+
+    main = run(LATTICE, llb.LLB_SCHEME_MOMENT, ClockSampler(local))
+    extra = {}
+    if not args.no_extra:
+        extra["population_d3q19"] = run(19, llb.LLB_SCHEME_POPULATION)
+        extra["moment_d3q27"] = run(27, llb.LLB_SCHEME_MOMENT)
+        extra["population_d3q27"] = run(27, llb.LLB_SCHEME_POPULATION)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = e2e_arm(args, llb, rho, u, stream, world)
+
+    # diagnostics pass (off the step path; reported separately)
+    ctx = make_ctx(llb, LATTICE, llb.LLB_SCHEME_MOMENT, stream)
+    try:
+        llb.llb_init_equilibrium(ctx, rho, u)
+        llb.llb_step(ctx, 2)
+        llb.llb_diagnostics(ctx)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            diag = llb.llb_diagnostics(ctx)
+        diag_ms = (time.perf_counter() - t0) / 5 * 1e3
+    finally:
+        llb.llb_destroy(ctx)
+    return main, extra, e2e, {"ms": diag_ms, "mass": diag["mass"][0], "flags": diag["flags"]}, peak, peak_src
+
+
+def e2e_arm(args, llb, rho, u, stream, world):
+    """Per step: pinned host canonical FP32 moments -> device, one step, device -> pinned host."""
+    import torch
+
+    nodes = NX * NY * NZ
+    ctx = make_ctx(llb, LATTICE, llb.LLB_SCHEME_MOMENT, stream)
+    try:
+        llb.llb_init_equilibrium(ctx, rho, u)
+        dev = torch.empty((10, NZ, NY, NX), dtype=torch.float32, device="cuda")
+        llb.llb_get_moments_device(ctx, dev)
+        h_in = torch.empty((10, NZ, NY, NX), dtype=torch.float32, pin_memory=True)
+        h_out = torch.empty_like(h_in).pin_memory()
+        h_in.copy_(dev)
+        torch.cuda.synchronize()
+        k = max(1, args.e2e_steps)
+        for _ in range(2):
+            llb.llb_init_moments(ctx, h_in)
+            llb.llb_step(ctx, 1)
+            llb.llb_get_moments(ctx, h_out)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            llb.llb_init_moments(ctx, h_in)
+            llb.llb_step(ctx, 1)
+            llb.llb_get_moments(ctx, h_out)
+        torch.cuda.synchronize()
+        dt = reduce_max(time.perf_counter() - t0, world)
+    finally:
+        llb.llb_destroy(ctx)
+    nbytes = 10 * nodes * 4
+    return {"value": world * nodes * k / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": k,
+            "path": "llb_init_moments(host) + llb_step(1) + llb_get_moments(host), FP32 canonical, pinned"}
+
+
+# ----------------------------------------------------------------------------- CPU (oracle) legs
+
+
+def oracle_sample(nz_sample):
+    """The bench field restricted to a 256 x 256 x nz_sample periodic slab."""
+    from paper_2301_01622_gb300 import inputs
+    rho, u = inputs.taylor_green_3d(NX, NY, NZ, u0=U0, noise=NOISE, seed=SEED)
+    return rho[:nz_sample].copy(), u[:, :nz_sample].copy()
+
+
+def cpu_baseline(gpu_check: bool):
+    """Time the FP64 oracle on one full-size step (the bench field), and use its
+    result to check the GPU's first step at FP32 tolerance."""
+    from oracle import D3Q19, lb
+    from paper_2301_01622_gb300 import inputs, llb
+
+    rho, u = inputs.taylor_green_3d(NX, NY, NZ, u0=U0, noise=NOISE, seed=SEED)
+    m0 = lb.equilibrium_moments(rho, u)
+    t0 = time.perf_counter()
+    ref = lb.step_moment_only(m0, D3Q19, TAU)
+    dt = time.perf_counter() - t0
+    out = {"value": NX * NY * NZ / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": "one time step of the full 256^3 D3Q19 workload, numpy FP64, single thread",
+           "seconds": dt}
+    parity = None
+    if gpu_check:
+        import torch
+        ctx = make_ctx(llb, LATTICE, llb.LLB_SCHEME_MOMENT, torch.cuda.current_stream().cuda_stream)
+        try:
+            llb.llb_init_equilibrium(ctx, rho, u)
+            llb.llb_step(ctx, 1)
+            got = llb.llb_get_moments(ctx, np.empty((10, NZ, NY, NX)))
+        finally:
+            llb.llb_destroy(ctx)
+        errs = {}
+        for name, sl in (("rho", slice(0, 1)), ("j", slice(1, 4)), ("P", slice(4, 10))):
+            errs[name] = float(np.abs(got[sl] - ref[sl]).max() / np.abs(ref[sl]).max())
+        parity = {"max_rel_err": errs, "tol": 1e-5, "pass": all(v <= 1e-5 for v in errs.values()),
+                  "vs": "FP64 oracle, one step of the full 256^3 field"}
+    return out, parity
+
+
+def reference_arm(args, rank):
+    """The oracle as it stands, on the host cores, on this arm's workload: each
+    step is one time step of a 256 x 256 x nz periodic slab of the bench field,
+    nz chosen so the whole run ends within a few minutes."""
+    from oracle import D3Q19, lb
+
+    if rank != 0:
+        return None
+    budget_s = 150.0
+    per_plane = 0.03
+    nzs = int(max(1, min(NZ, budget_s / max(1, args.steps + args.warmup) / per_plane)))
+    rho, u = oracle_sample(nzs)
+    m = lb.equilibrium_moments(rho, u)
+    for _ in range(args.warmup):
+        m = lb.step_moment_only(m, D3Q19, TAU)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m = lb.step_moment_only(m, D3Q19, TAU)
+    dt = time.perf_counter() - t0
+    nodes = NX * NY * nzs
+    val = nodes * args.steps / dt / 1e6
+    sample = f"each step: one time step of a 256x256x{nzs} periodic slab of the workload (numpy FP64 oracle, 1 thread)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_nodes_per_step": nodes},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ----------------------------------------------------------------------------- main
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = reference_arm(args, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    main_r, extra, e2e, diag, peak, peak_src = gpu_arm(args, rank, world, local)
+    cpu, parity = (None, None)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, parity = cpu_baseline(gpu_check=True)
+
+    if rank != 0:
+        return
+    nodes = NX * NY * NZ
+    traffic = ncu_traffic("moment_tiled_d3q19_f32")
+    roof = {"bound": "hbm", "achieved": main_r["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": main_r["achieved_gbs"] / peak, "traffic": traffic,
+            "peak_source": peak_src + ", burst copy figure (the step kernel is timed alone)",
+            "algorithmic_bytes_per_launch": main_r["bytes_per_node"] * nodes,
+            "kernel": "k_moment_tiled<D3Q19,float,32,8>", "avg_launch_ms": main_r["launch_ms"]}
+    line = {
+        "metric": METRIC, "value": main_r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes_per_gpu": nodes, "lattice": "D3Q19", "tau": TAU,
+                   "parallelism": "replicas" if world > 1 else "single", "l2": L2_NOTE},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": main_r["clocks"],
+        "parity": parity,
+        "population_d3q19": _short(extra.get("population_d3q19")),
+        "moment_d3q27": _short(extra.get("moment_d3q27")),
+        "population_d3q27": _short(extra.get("population_d3q27")),
+        "speedup_vs_population_d3q19": (main_r["mlups"] / extra["population_d3q19"]["mlups"])
+        if "population_d3q19" in extra else None,
+        "diagnostics": diag,
+        "paper_context": {"v100_mlups_without_populations": 622, "v100_mlups_with_populations": 277,
+                          "workload": "128^3 two-component droplet collision, Tesla V100 (not this workload)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _short(r):
+    if not r:
+        return None
+    return {"mlups": r["mlups"], "frac": r["frac"], "achieved_gbs": r["achieved_gbs"],
+            "bytes_per_node": r["bytes_per_node"], "ms_per_step": r["ms_per_step"]}
+
+
+if __name__ == "__main__":
+    main()
