@@ -396,12 +396,12 @@ def main():
     if rank != 0:
         return
     nodes = NX * NY * NZ
-    traffic = ncu_traffic("moment_tiled_d3q19_f32")
+    traffic = ncu_traffic("moment_tma_d3q19_f32")
     roof = {"bound": "hbm", "achieved": main_r["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": main_r["achieved_gbs"] / peak, "traffic": traffic,
             "peak_source": peak_src + ", burst copy figure (the step kernel is timed alone)",
             "algorithmic_bytes_per_launch": main_r["bytes_per_node"] * nodes,
-            "kernel": "k_moment_tiled<D3Q19,float,32,8>", "avg_launch_ms": main_r["launch_ms"]}
+            "kernel": {1: "k_moment_direct", 2: "k_moment_tiled", 3: "k_moment_tma"}.get(main_r["kernel"], "?") + "<D3Q19,float>", "avg_launch_ms": main_r["launch_ms"]}
     line = {
         "metric": METRIC, "value": main_r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_r["ms_per_step"], "higher_is_better": True,

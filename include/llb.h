@@ -79,7 +79,8 @@ extern "C" {
 /* ---- kernel choice for LLB_SCHEME_MOMENT ----------------------------- */
 #define LLB_KERNEL_AUTO   0  /* fastest available for the shape            */
 #define LLB_KERNEL_DIRECT 1  /* one thread per node, gathers Q neighbours  */
-#define LLB_KERNEL_TILED  2  /* z-marching shared-memory tile kernel       */
+#define LLB_KERNEL_TILED  2  /* z-marching shared-memory tile kernel, plain loads */
+#define LLB_KERNEL_TMA    3  /* same tile kernel, planes staged by TMA box loads  */
 
 typedef struct llb_ctx llb_ctx;
 
@@ -132,7 +133,9 @@ LLB_API void llb_params_default(llb_params* p);
 LLB_API int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p,
                         llb_footprint* out);
 
-/* Bytes of one state copy (what each of llb_params.buffers must hold). */
+/* Bytes of one state copy (what each of llb_params.buffers must hold).  The
+ * moment-only state is stored with periodic ghost rows and columns, so this
+ * is slightly more than fields * nodes * element size. */
 LLB_API int llb_state_bytes(int nx, int ny, int nz, int lattice, const llb_params* p, size_t* out);
 
 /* Create a context for an nx * ny * nz periodic box on the current CUDA

@@ -66,7 +66,8 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     if (p.scheme != LLB_SCHEME_MOMENT && p.scheme != LLB_SCHEME_POPULATION && p.scheme != LLB_SCHEME_POPULATION_BGK) {
         *why = "unknown scheme"; return LLB_EINVAL;
     }
-    if (p.kernel != LLB_KERNEL_AUTO && p.kernel != LLB_KERNEL_DIRECT && p.kernel != LLB_KERNEL_TILED) {
+    if (p.kernel != LLB_KERNEL_AUTO && p.kernel != LLB_KERNEL_DIRECT && p.kernel != LLB_KERNEL_TILED &&
+        p.kernel != LLB_KERNEL_TMA) {
         *why = "unknown kernel"; return LLB_EINVAL;
     }
     if (p.ncomp == 2) {
@@ -87,6 +88,11 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     c->N = (size_t)nx * ny * nz;
     c->nf = fields_of(*c);
     c->elem = elem_size(p.storage);
+    // the moment-only state carries periodic ghosts (TMA tile boxes); the
+    // population schemes keep dense populations and dense moment temporaries
+    c->lay = make_layout(nx, ny, nz, c->scheme == LLB_SCHEME_MOMENT);
+    c->state_bytes = c->scheme == LLB_SCHEME_MOMENT ? (size_t)c->nf * c->lay.fs * c->elem
+                                                    : (size_t)c->nf * c->N * c->elem;
     return LLB_OK;
 }
 
@@ -131,6 +137,18 @@ int finish_init(llb_ctx* c, void* mom) {
 // Where the init kernels write shifted moments before finish_init.
 void* init_target(llb_ctx* c) {
     return c->scheme == LLB_SCHEME_MOMENT ? c->buf[c->cur] : c->buf[1 - c->cur];
+}
+
+// A kernel whose bounded wait gave up leaves a non-zero word at err_dev.
+int check_kernel_error(llb_ctx* c) {
+    int err = 0;
+    LLB_CUDA(c, cudaMemcpyAsync(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error word copy");
+    LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
+    if (err) {
+        c->sticky = LLB_ETIMEOUT;
+        return fail(c, LLB_ETIMEOUT, "a device wait gave up (TMA load did not complete)");
+    }
+    return LLB_OK;
 }
 
 int check_bad_flag(llb_ctx* c) {
@@ -179,7 +197,8 @@ int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p
     out->fields = c.nf;
     out->arrays = 2 * c.nf;
     out->bytes_per_node = 2 * (size_t)c.nf * c.elem;
-    out->state_bytes = (size_t)c.nf * c.elem * c.N;
+    out->state_bytes = c.scheme == LLB_SCHEME_MOMENT ? (size_t)c.nf * c.lay.fs * c.elem
+                                                     : (size_t)c.nf * c.N * c.elem;
     out->stream_bytes_per_node = 2 * (size_t)c.nf * c.elem;
     return LLB_OK;
 }
@@ -216,7 +235,7 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
         cudaGetLastError();
         return bail(LLB_ECUDA);
     }
-    const size_t bytes = (size_t)c->nf * c->elem * c->N;
+    const size_t bytes = c->state_bytes;
     for (int b = 0; b < 2; ++b) {
         if (prm.buffers[b]) {
             if (reinterpret_cast<uintptr_t>(prm.buffers[b]) % 256 != 0) return bail(LLB_EINVAL);
@@ -230,15 +249,20 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
     }
     c->diag_scratch_bytes = (size_t)diag_blocks(*c) * 8 * sizeof(double) + 256;
     if (cudaMalloc(&c->diag_scratch, c->diag_scratch_bytes + sizeof(llb_diag)) != cudaSuccess) { cudaGetLastError(); c->diag_scratch = nullptr; return bail(LLB_ENOMEM); }
-    if (cudaMalloc(&c->flag_dev, sizeof(int)) != cudaSuccess) { cudaGetLastError(); c->flag_dev = nullptr; return bail(LLB_ENOMEM); }
+    if (cudaMalloc(&c->flag_dev, 2 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); c->flag_dev = nullptr; return bail(LLB_ENOMEM); }
+    c->err_dev = static_cast<int*>(c->flag_dev) + 1;
+    if (cudaMemsetAsync(c->flag_dev, 0, 2 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
     if (c->scheme == LLB_SCHEME_MOMENT) {
-        if (c->kernel == LLB_KERNEL_AUTO || c->kernel == LLB_KERNEL_TILED) {
-            c->tile_ctas = moment_tiled_ctas(*c);
-            cudaGetLastError();
-            if (c->tile_ctas > 0) c->kernel = LLB_KERNEL_TILED;
-            else if (c->kernel == LLB_KERNEL_TILED) return bail(LLB_EINVAL);
-            else c->kernel = LLB_KERNEL_DIRECT;
-        }
+        c->tile_ctas = moment_tiled_ctas(*c);
+        cudaGetLastError();
+        c->tmap_ok = moment_tma_encode(*c, c->buf[0], &c->tmap[0]) && moment_tma_encode(*c, c->buf[1], &c->tmap[1]);
+        c->tma_ctas = c->tmap_ok ? moment_tma_ctas(*c) : 0;
+        cudaGetLastError();
+        const int want = c->kernel;
+        if (want == LLB_KERNEL_TMA && c->tma_ctas <= 0) return bail(LLB_EINVAL);
+        if (want == LLB_KERNEL_TILED && c->tile_ctas <= 0) return bail(LLB_EINVAL);
+        if (want == LLB_KERNEL_AUTO)
+            c->kernel = c->tma_ctas > 0 ? LLB_KERNEL_TMA : c->tile_ctas > 0 ? LLB_KERNEL_TILED : LLB_KERNEL_DIRECT;
     } else {
         c->kernel = LLB_KERNEL_DIRECT;
     }
@@ -308,7 +332,9 @@ int llb_step(llb_ctx* c, int nsteps) {
         void* out = c->buf[1 - c->cur];
         cudaError_t e;
         if (c->scheme == LLB_SCHEME_MOMENT)
-            e = c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out) : launch_moment_direct(*c, in, out);
+            e = c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, c->cur, out)
+                : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
+                                                : launch_moment_direct(*c, in, out);
         else
             e = launch_population_step(*c, in, out, c->scheme == LLB_SCHEME_POPULATION_BGK);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
@@ -330,7 +356,7 @@ int llb_get_moments(llb_ctx* c, void* host_out, int host_dtype) {
     LLB_CUDA(c, launch_shifted_to_canonical(*c, mom, c->staging, host_dtype), "convert");
     LLB_CUDA(c, cudaMemcpyAsync(host_out, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H moments");
     LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
-    return LLB_OK;
+    return check_kernel_error(c);
 }
 
 int llb_get_moments_device(llb_ctx* c, void* dev_out, int dtype) {
@@ -353,13 +379,13 @@ int llb_diagnostics(llb_ctx* c, llb_diag* out) {
     LLB_CUDA(c, launch_diagnostics(*c, mom, c->diag_scratch, dev_out), "diagnostics");
     LLB_CUDA(c, cudaMemcpyAsync(out, dev_out, sizeof(llb_diag), cudaMemcpyDeviceToHost, c->stream), "D2H diag");
     LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
-    return LLB_OK;
+    return check_kernel_error(c);
 }
 
 int llb_synchronize(llb_ctx* c) {
     LLB_CHECK_CTX(c);
     LLB_CUDA(c, cudaStreamSynchronize(c->stream), "synchronize");
-    return LLB_OK;
+    return check_kernel_error(c);
 }
 
 int llb_steps_done(const llb_ctx* c, long long* out) {

@@ -5,10 +5,14 @@
 // shifted storage:           d = rho - 1, j, A = P - cs^2 rho I
 // Equilibrium (second moment of Eq. eq-part): P^eq = cs^2 rho I + rho u u, so
 // A^eq = rho u u.  All conversions compute in FP64 and round once.
+// Canonical buffers are dense; the shifted state follows the context's
+// Layout (padded with periodic ghosts for the moment scheme), and every
+// write to it also writes the node's ghost copies.
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "lattice.cuh"
+#include "layout.cuh"
 
 namespace llb {
 namespace {
@@ -29,9 +33,26 @@ __device__ __forceinline__ void wrt(void* p, size_t i, int dt, double v) {
 
 __device__ __forceinline__ bool bad_rho(double r) { return !(r > 0.0) || !isfinite(r); }
 
+__device__ __forceinline__ void decode(const Layout& L, size_t i, int& x, int& y, int& z) {
+    x = (int)(i % L.nx);
+    const size_t r = i / L.nx;
+    y = (int)(r % L.ny);
+    z = (int)(r / L.ny);
+}
+
 template <class T>
-__global__ void k_canon_to_shifted(const void* __restrict__ canon, int cdt, T* __restrict__ st, size_t N,
+__device__ __forceinline__ void put(T* __restrict__ st, const Layout& L, int x, int y, int z, const double* v) {
+    for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
+        const size_t j = L.at(gx, gy, z);
+#pragma unroll
+        for (int f = 0; f < 10; ++f) st[f * L.fs + j] = (T)v[f];
+    });
+}
+
+template <class T>
+__global__ void k_canon_to_shifted(const void* __restrict__ canon, int cdt, T* __restrict__ st, Layout L,
                                    int* bad) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
         double v[10];
 #pragma unroll
@@ -41,47 +62,42 @@ __global__ void k_canon_to_shifted(const void* __restrict__ canon, int cdt, T* _
         for (int f = 1; f < 10; ++f) b = b || !isfinite(v[f]);
         if (b && bad) atomicOr(bad, 1);
         const double rho = v[0];
-        st[i] = (T)(rho - 1.0);
-        st[N + i] = (T)v[1];
-        st[2 * N + i] = (T)v[2];
-        st[3 * N + i] = (T)v[3];
-        st[4 * N + i] = (T)(v[4] - kCs2 * rho);
-        st[5 * N + i] = (T)(v[5] - kCs2 * rho);
-        st[6 * N + i] = (T)(v[6] - kCs2 * rho);
-        st[7 * N + i] = (T)v[7];
-        st[8 * N + i] = (T)v[8];
-        st[9 * N + i] = (T)v[9];
+        const double o[10] = {rho - 1.0, v[1], v[2], v[3], v[4] - kCs2 * rho, v[5] - kCs2 * rho,
+                              v[6] - kCs2 * rho, v[7], v[8], v[9]};
+        int x, y, z;
+        decode(L, i, x, y, z);
+        put(st, L, x, y, z, o);
     }
 }
 
 template <class T>
-__global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ canon, int cdt, size_t N) {
+__global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-        const double rho = 1.0 + (double)st[i];
+        int x, y, z;
+        decode(L, i, x, y, z);
+        const size_t j = L.at(x, y, z);
+        const double rho = 1.0 + (double)st[j];
         wrt(canon, i, cdt, rho);
-        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, (double)st[f * N + i]);
-        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, (double)st[f * N + i] + kCs2 * rho);
-        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, (double)st[f * N + i]);
+        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
+        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j] + kCs2 * rho);
+        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
     }
 }
 
 template <class T>
 __global__ void k_equilibrium(const void* __restrict__ rho_p, const void* __restrict__ u_p, int dt,
-                              T* __restrict__ st, size_t N, int* bad) {
+                              T* __restrict__ st, Layout L, int* bad) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
         const double rho = rdt(rho_p, i, dt);
         const double ux = rdt(u_p, i, dt), uy = rdt(u_p, N + i, dt), uz = rdt(u_p, 2 * N + i, dt);
         if ((bad_rho(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) && bad) atomicOr(bad, 1);
-        st[i] = (T)(rho - 1.0);
-        st[N + i] = (T)(rho * ux);
-        st[2 * N + i] = (T)(rho * uy);
-        st[3 * N + i] = (T)(rho * uz);
-        st[4 * N + i] = (T)(rho * ux * ux);
-        st[5 * N + i] = (T)(rho * uy * uy);
-        st[6 * N + i] = (T)(rho * uz * uz);
-        st[7 * N + i] = (T)(rho * ux * uy);
-        st[8 * N + i] = (T)(rho * ux * uz);
-        st[9 * N + i] = (T)(rho * uy * uz);
+        const double o[10] = {rho - 1.0, rho * ux, rho * uy, rho * uz, rho * ux * ux, rho * uy * uy,
+                              rho * uz * uz, rho * ux * uy, rho * ux * uz, rho * uy * uz};
+        int x, y, z;
+        decode(L, i, x, y, z);
+        put(st, L, x, y, z, o);
     }
 }
 
@@ -95,25 +111,25 @@ int grid_for(const llb_ctx& c) {
 
 cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int cdt, void* st, int* bad) {
     if (c.storage == LLB_F64)
-        k_canon_to_shifted<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.N, bad);
+        k_canon_to_shifted<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
     else
-        k_canon_to_shifted<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.N, bad);
+        k_canon_to_shifted<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* canon, int cdt) {
     if (c.storage == LLB_F64)
-        k_shifted_to_canon<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.N);
+        k_shifted_to_canon<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
     else
-        k_shifted_to_canon<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.N);
+        k_shifted_to_canon<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay);
     return cudaGetLastError();
 }
 
 cudaError_t launch_equilibrium(const llb_ctx& c, const void* rho, const void* u, int dt, void* st, int* bad) {
     if (c.storage == LLB_F64)
-        k_equilibrium<double><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<double*>(st), c.N, bad);
+        k_equilibrium<double><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<double*>(st), c.lay, bad);
     else
-        k_equilibrium<float><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<float*>(st), c.N, bad);
+        k_equilibrium<float><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<float*>(st), c.lay, bad);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 #include "internal.h"
 #include "lattice.cuh"
+#include "layout.cuh"
 
 namespace llb {
 namespace {
@@ -67,13 +68,17 @@ __device__ Part block_reduce(Part p) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restrict__ m, size_t N,
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restrict__ m, Layout L,
                                                                double* __restrict__ rows) {
     Part p;
     part_init(p);
-    for (size_t i = blockIdx.x * (size_t)kDiagThreads + threadIdx.x; i < N; i += (size_t)gridDim.x * kDiagThreads) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz, F = L.fs;
+    for (size_t n = blockIdx.x * (size_t)kDiagThreads + threadIdx.x; n < N; n += (size_t)gridDim.x * kDiagThreads) {
+        const int x = (int)(n % L.nx);
+        const size_t r = n / L.nx;
+        const size_t i = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
         const double d = (double)m[i];
-        const double jx = (double)m[N + i], jy = (double)m[2 * N + i], jz = (double)m[3 * N + i];
+        const double jx = (double)m[F + i], jy = (double)m[2 * F + i], jz = (double)m[3 * F + i];
         const double rho = 1.0 + d;
         p.v[0] += d;
         p.v[1] += jx;
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
         p.v[6] = fmin(p.v[6], rho);
         bool finite = isfinite(d) && isfinite(jx) && isfinite(jy) && isfinite(jz);
 #pragma unroll
-        for (int f = 4; f < 10; ++f) finite = finite && isfinite((double)m[f * N + i]);
+        for (int f = 4; f < 10; ++f) finite = finite && isfinite((double)m[f * F + i]);
         if (!finite) p.v[7] = 1.0;
     }
     p = block_reduce(p);
@@ -132,9 +137,9 @@ cudaError_t launch_diagnostics(const llb_ctx& c, const void* mom, void* scratch,
     const int nb = diag_blocks(c);
     double* rows = static_cast<double*>(scratch);
     if (c.storage == LLB_F64)
-        k_diag_partial<double><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.N, rows);
+        k_diag_partial<double><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.lay, rows);
     else
-        k_diag_partial<float><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const float*>(mom), c.N, rows);
+        k_diag_partial<float><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const float*>(mom), c.lay, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_diag_final<<<1, kDiagThreads, 0, c.stream>>>(rows, nb, c.N, dev_out);

@@ -1,6 +1,7 @@
 // Internal context and launcher declarations of libllb (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -8,6 +9,7 @@
 #include <string>
 
 #include "../../include/llb.h"
+#include "layout.cuh"
 
 struct llb_ctx {
     int nx = 0, ny = 0, nz = 0;
@@ -24,6 +26,12 @@ struct llb_ctx {
     size_t N = 0;            // nodes
     int nf = 0;              // arrays per state copy
     size_t elem = 4;         // bytes per element of the state
+    size_t state_bytes = 0;  // bytes of one state copy
+    llb::Layout lay{};       // layout of moment-format buffers (state of the moment scheme,
+                             // temporaries of the population schemes)
+    CUtensorMap tmap[2];     // TMA descriptors of buf[0], buf[1] (moment scheme)
+    bool tmap_ok = false;
+    void* err_dev = nullptr; // device int: set by a kernel whose bounded wait gave up
     void* buf[2] = {nullptr, nullptr};
     bool owns[2] = {false, false};
     int cur = 0;             // buf[cur] holds the state at time t
@@ -36,8 +44,9 @@ struct llb_ctx {
     long long t = 0;
     int sticky = LLB_OK;
     std::string msg;
-    // tiled-kernel launch plan
+    // persistent launch plans (grid sizes), 0 = kernel unusable for this shape
     int tile_ctas = 0;
+    int tma_ctas = 0;
 };
 
 namespace llb {
@@ -49,7 +58,11 @@ int canonical_fields(const llb_ctx& c);    // 10 or 11
 // Moment-only, one component (moment_step.cu)
 cudaError_t launch_moment_direct(const llb_ctx& c, const void* in, void* out);
 cudaError_t launch_moment_tiled(const llb_ctx& c, const void* in, void* out);
+cudaError_t launch_moment_tma(const llb_ctx& c, int in_index, void* out);
 int moment_tiled_ctas(const llb_ctx& c);   // persistent grid size, 0 if the kernel cannot run
+int moment_tma_ctas(const llb_ctx& c);
+// Encode the TMA descriptor of a moment buffer; false if TMA cannot serve this shape.
+bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out);
 
 // Population-storing baselines (population_step.cu)
 cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);

@@ -8,56 +8,74 @@
 //   4. projection (Eq. HYD):  d = sum g_i, j = sum g_i c_i, A = sum g_i c_i c_i - cs^2 d I
 // No population is ever stored in global memory (Sec. III A, "without arrays").
 //
-// Two kernels:
+// Three kernels:
 //   * k_moment_direct: one thread per output node, gathers the ten moments of
 //     each of its Q neighbours and repeats the collision per neighbour.
-//     Simple and shape-agnostic; the reference GPU path.
-//   * k_moment_tiled: persistent z-marching kernel.  A CTA owns a BX x BY
-//     column of output nodes and walks it plane by plane.  For every source
-//     plane it collides each node of the tile plus a one-node halo ONCE,
-//     evaluates the Q-3 populations that cross to another column and
-//     publishes them in shared memory; each output thread then pulls one
+//     Shape-agnostic; the reference GPU path.
+//   * k_moment_tiled: persistent z-marching kernel with plain loads.  A CTA
+//     owns a BX x BY column of output nodes and walks it plane by plane.  For
+//     every source plane it collides each node of the tile plus a one-node
+//     halo ONCE, evaluates the Q-3 populations that cross to another column
+//     and publishes them in shared memory; each output thread then pulls one
 //     scalar per direction (instead of ten moments) and adds it into one of
-//     three rolling per-plane accumulators (planes s-1, s, s+1), so that each
-//     moment is read from and written to HBM once per step.
+//     three rolling per-plane accumulators (planes s-1, s, s+1).  Each moment
+//     is read from and written to HBM once per step.
+//   * k_moment_tma: the same computation, with the tile-plus-halo moments of
+//     each source plane fetched by one TMA box load into an NST-deep ring of
+//     shared-memory stages (mbarrier completion), so that several planes of
+//     loads are in flight per CTA without holding registers.  Needs the
+//     padded layout (periodic ghosts, 16-byte aligned tile start).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.h"
 #include "lattice.cuh"
+#include "layout.cuh"
+#include "tma.cuh"
 
 namespace llb {
 namespace {
 
+constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) before a TMA wait gives up
+
 template <class T>
-__device__ __forceinline__ Mom<T> load_mom(const T* __restrict__ p, size_t idx, size_t N) {
+__device__ __forceinline__ Mom<T> load_mom(const T* __restrict__ p, size_t idx, size_t fs) {
     Mom<T> m;
     m.d = __ldg(p + idx);
-    m.jx = __ldg(p + N + idx);
-    m.jy = __ldg(p + 2 * N + idx);
-    m.jz = __ldg(p + 3 * N + idx);
-    m.axx = __ldg(p + 4 * N + idx);
-    m.ayy = __ldg(p + 5 * N + idx);
-    m.azz = __ldg(p + 6 * N + idx);
-    m.axy = __ldg(p + 7 * N + idx);
-    m.axz = __ldg(p + 8 * N + idx);
-    m.ayz = __ldg(p + 9 * N + idx);
+    m.jx = __ldg(p + fs + idx);
+    m.jy = __ldg(p + 2 * fs + idx);
+    m.jz = __ldg(p + 3 * fs + idx);
+    m.axx = __ldg(p + 4 * fs + idx);
+    m.ayy = __ldg(p + 5 * fs + idx);
+    m.azz = __ldg(p + 6 * fs + idx);
+    m.axy = __ldg(p + 7 * fs + idx);
+    m.axz = __ldg(p + 8 * fs + idx);
+    m.ayz = __ldg(p + 9 * fs + idx);
     return m;
 }
 
 template <class T>
-__device__ __forceinline__ void store_mom(T* __restrict__ p, size_t idx, size_t N, const Mom<T>& m) {
+__device__ __forceinline__ void store_mom(T* __restrict__ p, size_t idx, size_t fs, const Mom<T>& m) {
     p[idx] = m.d;
-    p[N + idx] = m.jx;
-    p[2 * N + idx] = m.jy;
-    p[3 * N + idx] = m.jz;
-    p[4 * N + idx] = m.axx;
-    p[5 * N + idx] = m.ayy;
-    p[6 * N + idx] = m.azz;
-    p[7 * N + idx] = m.axy;
-    p[8 * N + idx] = m.axz;
-    p[9 * N + idx] = m.ayz;
+    p[fs + idx] = m.jx;
+    p[2 * fs + idx] = m.jy;
+    p[3 * fs + idx] = m.jz;
+    p[4 * fs + idx] = m.axx;
+    p[5 * fs + idx] = m.ayy;
+    p[6 * fs + idx] = m.azz;
+    p[7 * fs + idx] = m.axy;
+    p[8 * fs + idx] = m.axz;
+    p[9 * fs + idx] = m.ayz;
+}
+
+// Store node (x, y, z) and its periodic ghost copies.
+template <class T>
+__device__ __forceinline__ void store_node(T* __restrict__ p, const Layout& L, int x, int y, int z, const Mom<T>& m) {
+    for_node_and_ghosts(L, x, y, [&](int gx, int gy) { store_mom(p, L.at(gx, gy, z), L.fs, m); });
 }
 
 __device__ __forceinline__ int pmod(int v, int n) {
@@ -68,12 +86,12 @@ __device__ __forceinline__ int pmod(int v, int n) {
 // ---------------------------------------------------------------------------
 // Direct kernel: grid (ceil(nx/128), ny, nz), one thread per output node.
 template <class L, class T>
-__global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in, T* __restrict__ out, int nx,
-                                                       int ny, int nz, size_t N, T omega) {
+__global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in, T* __restrict__ out, Layout lay,
+                                                       T omega) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int z = blockIdx.z;
-    if (x >= nx) return;
+    if (x >= lay.nx) return;
     Acc<T> acc;
     acc.zero();
 #pragma unroll
@@ -83,26 +101,15 @@ __global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in,
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const int sx = wrap_idx(x - cx, nx), sy = wrap_idx(y - cy, ny), sz = wrap_idx(z - cz, nz);
-                const size_t s = ((size_t)sz * ny + sy) * nx + sx;
-                const Mom<T> c = collide(load_mom(in, s, N), omega);
+                const size_t s = lay.at(wrap_idx(x - cx, lay.nx), wrap_idx(y - cy, lay.ny), wrap_idx(z - cz, lay.nz));
+                const Mom<T> c = collide(load_mom(in, s, lay.fs), omega);
                 acc.add(g_dir<L, T>(c, g_shared(c), cx, cy, cz), cx, cy, cz);
             }
-    store_mom(out, ((size_t)z * ny + y) * nx + x, N, acc.finish());
+    store_node(out, lay, x, y, z, acc.finish());
 }
 
 // ---------------------------------------------------------------------------
-// Tiled z-marching kernel.
-template <class L, class T, int BX, int BY>
-struct Tiled {
-    static constexpr int NT = BX * BY;             // threads = output columns of a tile
-    static constexpr int HX = BX + 2, HY = BY + 2; // tile plus one-node halo
-    static constexpr int HN = HX * HY;
-    static constexpr int NH = HN - NT;             // halo nodes, one per thread t < NH
-    static constexpr int NS = n_xy_shifted<L>();   // directions crossing columns
-    static constexpr size_t smem_bytes = sizeof(T) * 2 * NS * HN;
-    static_assert(NH <= NT, "halo must fit one node per thread");
-};
+// Shared pieces of the two z-marching kernels.
 
 // Publish the column-crossing populations of one collided node into G[k][n].
 template <class L, class T, int HN>
@@ -121,32 +128,77 @@ __device__ __forceinline__ void publish(T* __restrict__ G, int n, const Mom<T>& 
             }
 }
 
+// Pull the crossing populations of output node n1 from G and add them to the
+// accumulators of planes s-1 (X), s (Y), s+1 (Z); the own-column populations
+// (c_x = c_y = 0) come from registers.
+template <class L, class T, int HN, int HX>
+__device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T g_0, T g_p, Acc<T>& X, Acc<T>& Y,
+                                       Acc<T>& Z) {
+    Z.zero();
+    int k = 0;
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx) {
+                if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0)) continue;
+                const T g = G[k * HN + n1 - cy * HX - cx];
+                if (cz < 0) X.add(g, cx, cy, cz);
+                else if (cz == 0) Y.add(g, cx, cy, cz);
+                else Z.add(g, cx, cy, cz);
+                ++k;
+            }
+    X.add(g_m, 0, 0, -1);
+    Y.add(g_0, 0, 0, 0);
+    Z.add(g_p, 0, 0, 1);
+}
+
+// Halo node handled by thread t < NH: top row, bottom row, then side columns.
+template <int BX, int BY>
+__device__ __forceinline__ void halo_node(int t, int& hx, int& hy) {
+    constexpr int HX = BX + 2;
+    if (t < HX) {
+        hx = t; hy = 0;
+    } else if (t < 2 * HX) {
+        hx = t - HX; hy = BY + 1;
+    } else {
+        const int k = t - 2 * HX;
+        hy = 1 + (k >> 1);
+        hx = (k & 1) ? (BX + 1) : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled z-marching kernel, plain loads.
+template <class L, class T, int BX, int BY>
+struct Tiled {
+    static constexpr int NT = BX * BY;             // threads = output columns of a tile
+    static constexpr int HX = BX + 2, HY = BY + 2; // tile plus one-node halo
+    static constexpr int HN = HX * HY;
+    static constexpr int NH = HN - NT;             // halo nodes, one per thread t < NH
+    static constexpr int NS = n_xy_shifted<L>();   // directions crossing columns
+    static constexpr size_t smem_bytes = sizeof(T) * 2 * NS * HN;
+    static_assert(NH <= NT, "halo must fit one node per thread");
+};
+
 template <class L, class T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY, 2)
-    k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz, size_t N, T omega,
-                   int ncx, long long W) {
+    k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, T omega, int ncx, long long W) {
     using K = Tiled<L, T, BX, BY>;
     constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const Gbase = reinterpret_cast<T*>(smem_raw);
+    const int nx = lay.nx, ny = lay.ny, nz = lay.nz;
 
     const int t = threadIdx.x;
     const int tx = t % BX, ty = t / BX;
-    const int n1 = (ty + 1) * HX + (tx + 1);  // own node, halo coordinates
-    // halo node handled by this thread (if t < NH): top row, bottom row, then side columns
+    const int n1 = (ty + 1) * HX + (tx + 1);
     const bool has2 = t < NH;
-    int hx2 = 0, hy2 = 0;
-    if (t < HX) {
-        hx2 = t; hy2 = 0;
-    } else if (t < 2 * HX) {
-        hx2 = t - HX; hy2 = BY + 1;
-    } else {
-        const int k = t - 2 * HX;
-        hy2 = 1 + (k >> 1);
-        hx2 = (k & 1) ? (BX + 1) : 0;
-    }
+    int hx2, hy2;
+    halo_node<BX, BY>(t, hx2, hy2);
     const int n2 = hy2 * HX + hx2;
-    const size_t plane = (size_t)nx * ny;
+    const size_t plane = (size_t)lay.px * lay.py;
 
     const long long w0 = (long long)blockIdx.x * W / gridDim.x;
     const long long w1 = (long long)(blockIdx.x + 1) * W / gridDim.x;
@@ -159,29 +211,26 @@ __global__ void __launch_bounds__(BX * BY, 2)
         const int zb = za + (int)(wend - w);  // outputs za .. zb-1
         w = wend;
         const int x0 = (col % ncx) * BX, y0 = (col / ncx) * BY;
-        const size_t off1 = (size_t)pmod(y0 + ty, ny) * nx + pmod(x0 + tx, nx);
-        const size_t off2 = (size_t)pmod(y0 - 1 + hy2, ny) * nx + pmod(x0 - 1 + hx2, nx);
+        const size_t off1 = lay.at(pmod(x0 + tx, nx), pmod(y0 + ty, ny), 0);
+        const size_t off2 = lay.at(pmod(x0 - 1 + hx2, nx), pmod(y0 - 1 + hy2, ny), 0);
         const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
 
         int zs = pmod(za - 1, nz);
-        Mom<T> m1 = load_mom(in, zs * plane + off1, N);
-        Mom<T> m2;
-        if (has2) m2 = load_mom(in, zs * plane + off2, N);
+        Mom<T> m1 = load_mom(in, zs * plane + off1, lay.fs);
+        Mom<T> m2 = m1;
+        if (has2) m2 = load_mom(in, zs * plane + off2, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
 
-        // One source plane s: X collects plane s-1 (complete afterwards),
-        // Y plane s, Z plane s+1 (started here).
         auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) {
             T* const G = Gbase + buf * (NS * HN);
-            // prefetch source plane s+1
-            Mom<T> p1, p2;
+            Mom<T> p1 = m1, p2 = m2;
             const bool more = s + 1 <= zb;
             if (more) {
                 const size_t zo = (size_t)pmod(s + 1, nz) * plane;
-                p1 = load_mom(in, zo + off1, N);
-                if (has2) p2 = load_mom(in, zo + off2, N);
+                p1 = load_mom(in, zo + off1, lay.fs);
+                if (has2) p2 = load_mom(in, zo + off2, lay.fs);
             }
             const Mom<T> c1 = collide(m1, omega);
             publish<L, T, HN>(G, n1, c1);
@@ -191,30 +240,11 @@ __global__ void __launch_bounds__(BX * BY, 2)
             const T g_p = g_dir<L, T>(c1, s01, 0, 0, 1);
             if (has2) publish<L, T, HN>(G, n2, collide(m2, omega));
             __syncthreads();
-            Z.zero();
-            int k = 0;
-#pragma unroll
-            for (int cz = -1; cz <= 1; ++cz)
-#pragma unroll
-                for (int cy = -1; cy <= 1; ++cy)
-#pragma unroll
-                    for (int cx = -1; cx <= 1; ++cx) {
-                        if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0)) continue;
-                        const T g = G[k * HN + n1 - cy * HX - cx];
-                        if (cz < 0) X.add(g, cx, cy, cz);
-                        else if (cz == 0) Y.add(g, cx, cy, cz);
-                        else Z.add(g, cx, cy, cz);
-                        ++k;
-                    }
-            X.add(g_m, 0, 0, -1);
-            Y.add(g_0, 0, 0, 0);
-            Z.add(g_p, 0, 0, 1);
-            if (s - 1 >= za && store_ok) store_mom(out, (size_t)(s - 1) * plane + off1, N, X.finish());
+            gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
+            if (s - 1 >= za && store_ok) store_node(out, lay, x0 + tx, y0 + ty, s - 1, X.finish());
             buf ^= 1;
-            if (more) {
-                m1 = p1;
-                if (has2) m2 = p2;
-            }
+            m1 = p1;
+            m2 = p2;
         };
 
         int s = za - 1;
@@ -232,13 +262,179 @@ __global__ void __launch_bounds__(BX * BY, 2)
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged z-marching kernel.
+template <class L, class T, int BX_, int BY_, int NST_>
+struct TmaCfg {
+    static constexpr int BX = BX_, BY = BY_, NST = NST_;
+    static constexpr int NT = BX * BY;
+    static constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY, NH = HN - NT;
+    static constexpr int NS = n_xy_shifted<L>();
+    static constexpr int SW = BX + 8;        // staged row: x0-4 .. x0+BX+3
+    static constexpr int SR = BY + 2;        // staged rows: y0-1 .. y0+BY
+    static constexpr int SF = SW * SR;       // elements per staged field
+    static constexpr int STAGE_BYTES = 10 * SF * (int)sizeof(T);
+    static constexpr int STAGE_STRIDE = (STAGE_BYTES + 1023) / 1024 * 1024;
+    static constexpr int G_OFF = NST * STAGE_STRIDE;
+    static constexpr int G_BYTES = 2 * NS * HN * (int)sizeof(T);
+    static constexpr int BAR_OFF = (G_OFF + G_BYTES + 7) / 8 * 8;
+    static constexpr int SMEM = BAR_OFF + 8 * NST + 1024;  // + slack to align the base to 1 KB
+    static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;    // CTAs per SM the register budget targets
+    static_assert(NH <= NT, "halo must fit one node per thread");
+    static_assert(SW * (int)sizeof(T) % 16 == 0, "TMA box row must be a multiple of 16 bytes");
+    static_assert(SW <= 256 && SR <= 256, "TMA box dimension limit");
+};
+
+template <class T, int SF, int SW>
+__device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int hy) {
+    const T* p = S + hy * SW + hx + 3;
+    Mom<T> m;
+    m.d = p[0];
+    m.jx = p[SF];
+    m.jy = p[2 * SF];
+    m.jz = p[3 * SF];
+    m.axx = p[4 * SF];
+    m.ayy = p[5 * SF];
+    m.azz = p[6 * SF];
+    m.axy = p[7 * SF];
+    m.axz = p[8 * SF];
+    m.ayz = p[9 * SF];
+    return m;
+}
+
+template <class L, class T, class C>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, int ncx,
+                 long long W, int* __restrict__ err) {
+    constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS, NH = C::NH;
+    constexpr int SF = C::SF, SW = C::SW;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    T* const Gbase = reinterpret_cast<T*>(smem + C::G_OFF);
+    const uint32_t stage0 = smem_u32(smem);
+    const uint32_t bar0 = smem_u32(smem + C::BAR_OFF);
+    const T* const S0 = reinterpret_cast<const T*>(smem);
+    const int nx = lay.nx, ny = lay.ny, nz = lay.nz;
+
+    const int t = threadIdx.x;
+    const int tx = t % BX, ty = t / BX;
+    const int n1 = (ty + 1) * HX + (tx + 1);
+    const bool has2 = t < NH;
+    int hx2, hy2;
+    halo_node<BX, BY>(t, hx2, hy2);
+    const int n2 = hy2 * HX + hx2;
+
+    if (t == 0) {
+        prefetch_tensormap(&tmap);
+        for (int k = 0; k < NST; ++k) mbar_init(bar0 + 8 * k, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    const long long w0 = (long long)blockIdx.x * W / gridDim.x;
+    const long long w1 = (long long)(blockIdx.x + 1) * W / gridDim.x;
+    int buf = 0;
+    unsigned q = 0;         // sequence number of the next source plane (all segments)
+    unsigned issued = 0;    // sequence numbers < issued have a TMA in flight or done (thread 0)
+
+    for (long long w = w0; w < w1;) {
+        const int col = (int)(w / nz);
+        const int za = (int)(w - (long long)col * nz);
+        const long long wend = min(w1, (long long)(col + 1) * nz);
+        const int zb = za + (int)(wend - w);  // outputs za .. zb-1
+        w = wend;
+        const int x0 = (col % ncx) * BX, y0 = (col / ncx) * BY;
+        const int P = zb - za + 2;            // source planes za-1 .. zb
+        const unsigned q0 = q;
+        const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
+
+        if (t == 0) {
+            for (int i = 0; i < NST && i < P; ++i) {
+                const unsigned qq = q0 + i;
+                const uint32_t bar = bar0 + 8 * (qq % NST);
+                mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
+                tma_load_4d(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, x0, y0, pmod(za - 1 + i, nz), 0, bar);
+            }
+            issued = q0 + min(NST, P);
+        }
+
+        Acc<T> a0, a1, a2;
+        a0.zero(); a1.zero(); a2.zero();
+
+        auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) -> bool {
+            const int k = q % NST;
+            const bool ok = mbar_wait_bounded(bar0 + 8 * k, (q / NST) & 1, kWaitBudget);
+            const T* const S = S0 + (size_t)k * (C::STAGE_STRIDE / sizeof(T));
+            T* const G = Gbase + buf * (NS * HN);
+            T g_m = T(0), g_0 = T(0), g_p = T(0);
+            if (ok) {
+                const Mom<T> c1 = collide(stage_mom<T, SF, SW>(S, tx + 1, ty + 1), omega);
+                publish<L, T, HN>(G, n1, c1);
+                const T s01 = g_shared(c1);
+                g_m = g_dir<L, T>(c1, s01, 0, 0, -1);
+                g_0 = g_dir<L, T>(c1, s01, 0, 0, 0);
+                g_p = g_dir<L, T>(c1, s01, 0, 0, 1);
+                if (has2) publish<L, T, HN>(G, n2, collide(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
+            }
+            if (__syncthreads_or(!ok)) return false;
+            // every thread is done with stage k: refill it with plane s + NST
+            if (t == 0 && (int)(q - q0) + NST < P) {
+                fence_proxy_async();
+                const unsigned qq = q + NST;
+                const uint32_t bar = bar0 + 8 * k;
+                mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
+                tma_load_4d(stage0 + k * C::STAGE_STRIDE, &tmap, x0, y0, pmod(s + NST, nz), 0, bar);
+                issued = qq + 1;
+            }
+            gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
+            if (s - 1 >= za && store_ok) store_node(out, lay, x0 + tx, y0 + ty, s - 1, X.finish());
+            buf ^= 1;
+            ++q;
+            return true;
+        };
+
+        bool alive = true;
+        int s = za - 1;
+        for (;;) {
+            if (s > zb) break;
+            if (!(alive = plane_step(s, a0, a1, a2))) break;
+            ++s;
+            if (s > zb) break;
+            if (!(alive = plane_step(s, a1, a2, a0))) break;
+            ++s;
+            if (s > zb) break;
+            if (!(alive = plane_step(s, a2, a0, a1))) break;
+            ++s;
+        }
+        if (!alive) {
+            // A wait gave up: report, let the loads still in flight land (bounded), leave.
+            if (t == 0) {
+                atomicExch(err, 1);
+                for (unsigned qq = q; qq < issued; ++qq)
+                    mbar_wait_bounded(bar0 + 8 * (qq % NST), (qq / NST) & 1, kWaitBudget);
+            }
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
 constexpr int kBX = 32, kBY = 8;
+
+template <class L, class T>
+struct TmaChoice {
+    // FP32: 4 stages of 16 KB; FP64 stages are twice as large, so 2.
+    using type = TmaCfg<L, T, 32, 8, (sizeof(T) == 4 ? 4 : 2)>;
+};
 
 template <class L, class T>
 cudaError_t run_direct(const llb_ctx& c, const void* in, void* out) {
     dim3 block(128), grid((c.nx + 127) / 128, c.ny, c.nz);
-    k_moment_direct<L, T><<<grid, block, 0, c.stream>>>(static_cast<const T*>(in), static_cast<T*>(out), c.nx,
-                                                         c.ny, c.nz, c.N, (T)c.omega);
+    k_moment_direct<L, T><<<grid, block, 0, c.stream>>>(static_cast<const T*>(in), static_cast<T*>(out), c.lay,
+                                                         (T)c.omega);
     return cudaGetLastError();
 }
 
@@ -253,37 +449,86 @@ int tiled_ctas(const llb_ctx& c) {
         per_sm < 1)
         return 0;
     const long long ncol = (long long)((c.nx + kBX - 1) / kBX) * ((c.ny + kBY - 1) / kBY);
-    const long long W = ncol * c.nz;
-    return (int)std::min<long long>(W, (long long)per_sm * c.num_sms);
+    return (int)std::min<long long>(ncol * c.nz, (long long)per_sm * c.num_sms);
 }
 
 template <class L, class T>
 cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) {
     using K = Tiled<L, T, kBX, kBY>;
     const int ncx = (c.nx + kBX - 1) / kBX;
-    const long long ncol = (long long)ncx * ((c.ny + kBY - 1) / kBY);
-    const long long W = ncol * c.nz;
-    const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
-    k_moment_tiled<L, T, kBX, kBY><<<grid, K::NT, K::smem_bytes, c.stream>>>(
-        static_cast<const T*>(in), static_cast<T*>(out), c.nx, c.ny, c.nz, c.N, (T)c.omega, ncx, W);
+    const long long W = (long long)ncx * ((c.ny + kBY - 1) / kBY) * c.nz;
+    k_moment_tiled<L, T, kBX, kBY><<<c.tile_ctas > 0 ? c.tile_ctas : 1, K::NT, K::smem_bytes, c.stream>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), c.lay, (T)c.omega, ncx, W);
     return cudaGetLastError();
+}
+
+template <class L, class T>
+int tma_ctas(const llb_ctx& c) {
+    using C = typename TmaChoice<L, T>::type;
+    if (!c.lay.ghosts || c.lay.px < C::SW || c.lay.py < C::SR) return 0;
+    auto kern = k_moment_tma<L, T, C>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM) != cudaSuccess || per_sm < 1)
+        return 0;
+    const long long ncol = (long long)((c.nx + C::BX - 1) / C::BX) * ((c.ny + C::BY - 1) / C::BY);
+    return (int)std::min<long long>(ncol * c.nz, (long long)per_sm * c.num_sms);
+}
+
+template <class L, class T>
+cudaError_t run_tma(const llb_ctx& c, int in_index, void* out) {
+    using C = typename TmaChoice<L, T>::type;
+    const int ncx = (c.nx + C::BX - 1) / C::BX;
+    const long long W = (long long)ncx * ((c.ny + C::BY - 1) / C::BY) * c.nz;
+    k_moment_tma<L, T, C><<<c.tma_ctas > 0 ? c.tma_ctas : 1, C::NT, C::SMEM, c.stream>>>(
+        c.tmap[in_index], static_cast<T*>(out), c.lay, (T)c.omega, ncx, W, static_cast<int*>(c.err_dev));
+    return cudaGetLastError();
+}
+
+template <class L, class T>
+bool tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
+    using C = typename TmaChoice<L, T>::type;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Layout& Lo = c.lay;
+    if (!Lo.ghosts) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)Lo.px, (cuuint64_t)Lo.py, (cuuint64_t)Lo.nz, 10};
+    const cuuint64_t strides[3] = {(cuuint64_t)Lo.px * sizeof(T), (cuuint64_t)Lo.px * Lo.py * sizeof(T),
+                                   (cuuint64_t)Lo.fs * sizeof(T)};
+    const cuuint32_t box[4] = {(cuuint32_t)C::SW, (cuuint32_t)C::SR, 1, 10};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(out, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 }  // namespace
 
+#define LLB_MDISPATCH(fn, ...)                                                                       \
+    (c.Q == 19 ? (c.storage == LLB_F64 ? fn<D3Q19, double>(__VA_ARGS__) : fn<D3Q19, float>(__VA_ARGS__)) \
+               : (c.storage == LLB_F64 ? fn<D3Q27, double>(__VA_ARGS__) : fn<D3Q27, float>(__VA_ARGS__)))
+
 cudaError_t launch_moment_direct(const llb_ctx& c, const void* in, void* out) {
-    if (c.Q == 19) return c.storage == LLB_F64 ? run_direct<D3Q19, double>(c, in, out) : run_direct<D3Q19, float>(c, in, out);
-    return c.storage == LLB_F64 ? run_direct<D3Q27, double>(c, in, out) : run_direct<D3Q27, float>(c, in, out);
+    return LLB_MDISPATCH(run_direct, c, in, out);
 }
-
-int moment_tiled_ctas(const llb_ctx& c) {
-    if (c.Q == 19) return c.storage == LLB_F64 ? tiled_ctas<D3Q19, double>(c) : tiled_ctas<D3Q19, float>(c);
-    return c.storage == LLB_F64 ? tiled_ctas<D3Q27, double>(c) : tiled_ctas<D3Q27, float>(c);
-}
-
+int moment_tiled_ctas(const llb_ctx& c) { return LLB_MDISPATCH(tiled_ctas, c); }
 cudaError_t launch_moment_tiled(const llb_ctx& c, const void* in, void* out) {
-    if (c.Q == 19) return c.storage == LLB_F64 ? run_tiled<D3Q19, double>(c, in, out) : run_tiled<D3Q19, float>(c, in, out);
-    return c.storage == LLB_F64 ? run_tiled<D3Q27, double>(c, in, out) : run_tiled<D3Q27, float>(c, in, out);
+    return LLB_MDISPATCH(run_tiled, c, in, out);
+}
+int moment_tma_ctas(const llb_ctx& c) { return LLB_MDISPATCH(tma_ctas, c); }
+cudaError_t launch_moment_tma(const llb_ctx& c, int in_index, void* out) {
+    return LLB_MDISPATCH(run_tma, c, in_index, out);
+}
+bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
+    return LLB_MDISPATCH(tma_encode, c, buf, out);
 }
 
 }  // namespace llb

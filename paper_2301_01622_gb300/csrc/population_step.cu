@@ -10,8 +10,9 @@
 //                the same map as the moment-only step;
 //   BGK:         f'_i = (1 - omega) f_i + omega h^eq_i (Eq. coll on the stored f_i),
 //                which keeps the ghost components.
-// The state holds shifted values g_i = f_i - w_i; direction k runs over
-// (cz, cy, cx) in {-1,0,1}^3 in that loop order, skipping absent vectors.
+// The state holds shifted values g_i = f_i - w_i in a dense [Q][N] layout;
+// direction k runs over (cz, cy, cx) in {-1,0,1}^3 in that loop order,
+// skipping absent vectors.  Moment temporaries follow the context's Layout.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(128) k_pop_step(const T* __restrict__ in, T* _
 // state_k(x) = g^R_k(m(x + c_k)): the population that a pull at x + c_k will read.
 template <class L, class T>
 __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st, int nx, int ny, int nz,
-                                   size_t N) {
+                                   size_t N, Layout lay) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
@@ -93,8 +94,8 @@ __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z + cz, nz) * ny + wrap_idx(y + cy, ny)) * nx + wrap_idx(x + cx, nx);
-                const Mom<T> m = load_mom(mom, s, N);
+                const size_t s = lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz));
+                const Mom<T> m = load_mom(mom, s, lay.fs);
                 st[(size_t)k * N + idx] = g_dir<L, T>(m, g_shared(m), cx, cy, cz);
                 ++k;
             }
@@ -102,7 +103,7 @@ __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st
 
 template <class L, class T>
 __global__ void k_moments_from_pop(const T* __restrict__ st, T* __restrict__ mom, int nx, int ny, int nz,
-                                   size_t N) {
+                                   size_t N, Layout lay) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
@@ -120,7 +121,7 @@ __global__ void k_moments_from_pop(const T* __restrict__ st, T* __restrict__ mom
                 acc.add(st[(size_t)k * N + s], cx, cy, cz);
                 ++k;
             }
-    store_mom(mom, ((size_t)z * ny + y) * nx + x, N, acc.finish());
+    store_mom(mom, lay.at(x, y, z), lay.fs, acc.finish());
 }
 
 dim3 node_grid(const llb_ctx& c) { return dim3((c.nx + 127) / 128, c.ny, c.nz); }
@@ -139,14 +140,14 @@ cudaError_t step_t(const llb_ctx& c, const void* in, void* out, bool bgk) {
 template <class L, class T>
 cudaError_t from_mom_t(const llb_ctx& c, const void* mom, void* st) {
     k_pop_from_moments<L, T><<<node_grid(c), 128, 0, c.stream>>>(static_cast<const T*>(mom), static_cast<T*>(st),
-                                                                  c.nx, c.ny, c.nz, c.N);
+                                                                  c.nx, c.ny, c.nz, c.N, c.lay);
     return cudaGetLastError();
 }
 
 template <class L, class T>
 cudaError_t to_mom_t(const llb_ctx& c, const void* st, void* mom) {
     k_moments_from_pop<L, T><<<node_grid(c), 128, 0, c.stream>>>(static_cast<const T*>(st), static_cast<T*>(mom),
-                                                                  c.nx, c.ny, c.nz, c.N);
+                                                                  c.nx, c.ny, c.nz, c.N, c.lay);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,14 @@ from gpu_helpers import assert_groups, run_gpu
 pytestmark = pytest.mark.gpu
 
 LAT = {19: D3Q19, 27: D3Q27}
-KERNELS = [llb.LLB_KERNEL_TILED, llb.LLB_KERNEL_DIRECT]
-KIDS = ["tiled", "direct"]
+KERNELS = [llb.LLB_KERNEL_TMA, llb.LLB_KERNEL_TILED, llb.LLB_KERNEL_DIRECT]
+KIDS = ["tma", "tiled", "direct"]
+
+
+def tma_fits(shape):
+    """The TMA kernel needs a padded row of >= 40 elements and >= 10 rows (tile 32 x 8 plus halo)."""
+    nx, ny, _ = shape
+    return ((nx + 8 + 7) // 8) * 8 >= 40 and ny + 2 >= 10
 
 
 @functools.lru_cache(maxsize=None)
@@ -58,7 +64,8 @@ def test_noisy_taylor_green_fp32_tau06(q):
     assert_groups(got, oracle_tg(q, n, tau, 200, 1e-3), 1e-5, what=f"D3Q{q} fp32 noisy")
 
 
-SHAPES = [(67, 45, 37), (33, 9, 5), (31, 17, 3), (5, 70, 2), (1, 1, 1), (2, 3, 4), (4, 4, 4), (64, 16, 8), (97, 1, 3)]
+SHAPES = [(67, 45, 37), (33, 9, 5), (31, 17, 3), (5, 70, 2), (1, 1, 1), (2, 3, 4), (4, 4, 4), (64, 16, 8), (97, 1, 3),
+          (25, 8, 1), (129, 40, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -68,9 +75,15 @@ def test_ragged_shapes_random_moments_fp64(shape, q, kernel):
     """Random non-equilibrium moments, shapes spanning several tiles, ragged
     tails and degenerate 1- and 2-node axes: 1e-12 after 3 steps."""
     nx, ny, nz = shape
+    if kernel == llb.LLB_KERNEL_TMA and not tma_fits(shape):
+        with pytest.raises(llb.LLBError) as e:
+            run_gpu(shape, q, 0.7, 1, m0=inputs.random_moments(nx, ny, nz, seed=1), kernel=kernel)
+        assert e.value.status == llb.LLB_EINVAL
+        return
     m0 = inputs.random_moments(nx, ny, nz, seed=nx * 10007 + ny * 101 + nz)
     ref = lb.run_moment_only(m0, LAT[q], 0.7, 3)
-    got, _ = run_gpu(shape, q, 0.7, 3, m0=m0, storage=llb.LLB_F64, kernel=kernel)
+    got, used = run_gpu(shape, q, 0.7, 3, m0=m0, storage=llb.LLB_F64, kernel=kernel)
+    assert used == kernel
     assert_groups(got, ref, 1e-12, what=f"{shape} D3Q{q}")
 
 
@@ -85,11 +98,14 @@ def test_zero_steps_round_trip(q):
 def test_tiled_is_deterministic_and_matches_direct(q):
     n = 40
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=5)
-    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
-    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
-    c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
+    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA)
+    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA)
+    c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
+    d, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
     assert np.array_equal(a, b)
-    assert_groups(a, c, 1e-6, what="tiled vs direct")
+    # the two z-marching kernels add the same terms in the same order
+    assert np.array_equal(a, c)
+    assert_groups(a, d, 1e-6, what="tiled vs direct")
 
 
 def _sample_nodes(nx, ny, nz, rng, count=60):
@@ -112,7 +128,7 @@ def test_full_size_256_sampled_nodes(q):
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=2301)
     m0 = lb.equilibrium_moments(rho, u)
     got, used = run_gpu((n, n, n), q, tau, 1, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_AUTO)
-    assert used == llb.LLB_KERNEL_TILED
+    assert used == llb.LLB_KERNEL_TMA
     rng = np.random.default_rng(q)
     pts = _sample_nodes(n, n, n, rng)
     ref = np.stack([lb.node_moment_only(m0, LAT[q], tau, x, y, z) for (x, y, z) in pts], axis=1)
