@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the D3Q27 and population lines")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tma", "tiled", "direct"],
+                    help="moment-only kernel (auto = the library's choice)")
     return ap.parse_args()
 
 
@@ -186,9 +188,14 @@ def ncu_traffic(key: str):
 # ----------------------------------------------------------------------------- GPU timing
 
 
+KERNEL_CODE = {"auto": 0, "direct": 1, "tiled": 2, "tma": 3}
+_KERNEL = ["auto"]
+
+
 def make_ctx(llb, lattice, scheme, stream, storage=None):
+    kern = KERNEL_CODE[_KERNEL[0]] if scheme == llb.LLB_SCHEME_MOMENT else 0
     p = llb.llb_params_default(storage=llb.LLB_F32 if storage is None else storage, scheme=scheme,
-                               stream=stream)
+                               stream=stream, kernel=kern)
     return llb.llb_create(NX, NY, NZ, lattice, TAU, p)
 
 
@@ -381,6 +388,7 @@ def reference_arm(args, rank):
 
 def main():
     args = parse()
+    _KERNEL[0] = args.kernel
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         line = reference_arm(args, rank)

@@ -6,14 +6,18 @@
 // Dense layout (xo = yo = 0, px = nx, py = ny): used for temporaries of the
 // population-storing schemes.
 //
-// Padded layout (moment-only state): xo = 4, yo = 1, px = nx + 8 rounded up
-// to a multiple of 8, py = ny + 2.  The extra columns and rows hold periodic
-// ghost copies -- column x = -1 holds x = nx-1, column x = nx holds x = 0,
-// row y = -1 holds y = ny-1, row y = ny holds y = 0 (corners likewise) --
-// written by every kernel that writes the state.  With them, the tile plus
-// halo that a CTA needs is one rectangular box whose x start is 16-byte
-// aligned, so one TMA load fetches it without wrapping; the three columns
-// x = -4..-2 and x > nx are padding that is never read as data.
+// Padded layout (moment-only state): xo = 8, yo = gy (1 or 2), px = nx + 16
+// rounded up to a multiple of 8, py = ny + 2 gy.  Node x = 0 then starts a
+// 32-byte sector in FP32 (64 bytes in FP64), so a warp that stores 32
+// consecutive nodes writes whole sectors and HBM never has to read a sector
+// back to merge a partial write.  The eight columns on each side and the gy
+// rows above and below hold periodic ghost copies: columns x = -8..-1 hold
+// x = nx-8..nx-1, columns x = nx..nx+7 hold x = 0..7, rows y = -gy..-1 hold
+// y = ny-gy..ny-1 and rows y = ny..ny+gy-1 hold y = 0..gy-1 (corners
+// likewise), written by every kernel that writes the state.  Whole sectors
+// of ghosts are written for the same reason.  With them the tile plus halo a
+// CTA needs is one rectangular box with a 16-byte aligned x start, so one
+// TMA load fetches it without wrapping.
 #pragma once
 
 #include <cstddef>
@@ -23,7 +27,7 @@ namespace llb {
 struct Layout {
     int nx, ny, nz;
     int px, py;   // row pitch (elements) and rows per plane
-    int xo, yo;   // offset of node (0, 0) inside a plane
+    int xo, yo;   // offset of node (0, 0) inside a plane; yo = ghost rows per side
     size_t fs;    // field stride in elements
     int ghosts;   // 1: periodic ghost copies are maintained
 
@@ -32,13 +36,15 @@ struct Layout {
     }
 };
 
-inline Layout make_layout(int nx, int ny, int nz, bool padded) {
+constexpr int kGhostX = 8;  // ghost columns per side (one FP32 sector)
+
+inline Layout make_layout(int nx, int ny, int nz, bool padded, int ghost_rows = 1) {
     Layout L;
     L.nx = nx; L.ny = ny; L.nz = nz;
     if (padded) {
-        L.xo = 4; L.yo = 1;
-        L.px = ((nx + 8 + 7) / 8) * 8;
-        L.py = ny + 2;
+        L.xo = kGhostX; L.yo = ghost_rows;
+        L.px = ((nx + 2 * kGhostX + 7) / 8) * 8;
+        L.py = ny + 2 * ghost_rows;
         L.ghosts = 1;
     } else {
         L.xo = 0; L.yo = 0;
@@ -50,22 +56,23 @@ inline Layout make_layout(int nx, int ny, int nz, bool padded) {
 }
 
 // Call fn(x', y') for (x, y) and, in a padded layout, for every ghost
-// position that mirrors (x, y) under the periodic wrap.
+// position that mirrors (x, y) under the periodic wrap: x' = x -+ nx inside
+// the ghost columns [-8, nx + 8), y' = y -+ ny inside the ghost rows.
 template <class F>
 __device__ __forceinline__ void for_node_and_ghosts(const Layout& L, int x, int y, F&& fn) {
     fn(x, y);
     if (!L.ghosts) return;
-    const bool gx0 = (x == 0), gx1 = (x == L.nx - 1);
-    const bool gy0 = (y == 0), gy1 = (y == L.ny - 1);
-    if (!(gx0 || gx1 || gy0 || gy1)) return;
+    const bool gxr = x < kGhostX, gxl = x >= L.nx - kGhostX;
+    const bool gyb = y < L.yo, gyt = y >= L.ny - L.yo;
+    if (!(gxr || gxl || gyb || gyt)) return;
     int xs[3], ys[3];
     int nxs = 0, nys = 0;
     xs[nxs++] = x;
-    if (gx0) xs[nxs++] = L.nx;
-    if (gx1) xs[nxs++] = -1;
+    if (gxr) xs[nxs++] = x + L.nx;
+    if (gxl) xs[nxs++] = x - L.nx;
     ys[nys++] = y;
-    if (gy0) ys[nys++] = L.ny;
-    if (gy1) ys[nys++] = -1;
+    if (gyb) ys[nys++] = y + L.ny;
+    if (gyt) ys[nys++] = y - L.ny;
     for (int a = 0; a < nys; ++a)
         for (int b = 0; b < nxs; ++b)
             if (a || b) fn(xs[b], ys[a]);

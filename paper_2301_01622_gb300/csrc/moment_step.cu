@@ -83,6 +83,50 @@ __device__ __forceinline__ int pmod(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Work of the z-marching kernels: items (z-chunk, xy-tile) in chunk-major
+// order, handed out round-robin to the persistent CTAs, so that the CTAs
+// resident at any moment hold neighbouring tiles of the same z-chunk and
+// march through z together -- the halo planes a CTA reads from its
+// neighbours' tiles were just fetched by them and are still in L2.
+struct Sched {
+    int ncx;      // tiles along x
+    int ntiles;   // tiles per z-chunk
+    int zc;       // planes per chunk (the last chunk may be shorter)
+    int nitems;   // ntiles * chunks
+
+    __device__ __forceinline__ void item(int it, int BX, int BY, int nz, int& x0, int& y0, int& za,
+                                         int& zb) const {
+        const int chunk = it / ntiles, tile = it - chunk * ntiles;
+        x0 = (tile % ncx) * BX;
+        y0 = (tile / ncx) * BY;
+        za = chunk * zc;
+        zb = min(nz, za + zc);
+    }
+};
+
+// Pick the chunk length that minimises rounds * (planes per item + 2 warm-up
+// planes) for `grid` persistent CTAs.
+Sched plan(int nx, int ny, int nz, int BX, int BY, int grid) {
+    Sched s;
+    s.ncx = (nx + BX - 1) / BX;
+    s.ntiles = s.ncx * ((ny + BY - 1) / BY);
+    long long best = -1;
+    for (int nch = 1; nch <= nz; ++nch) {
+        const int zc = (nz + nch - 1) / nch;
+        const int chunks = (nz + zc - 1) / zc;
+        const long long items = (long long)s.ntiles * chunks;
+        if (items > (1LL << 30)) break;
+        const long long rounds = (items + grid - 1) / grid;
+        const long long cost = rounds * (zc + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            s.zc = zc;
+            s.nitems = (int)items;
+        }
+    }
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // Direct kernel: grid (ceil(nx/128), ny, nz), one thread per output node.
 template <class L, class T>
@@ -184,7 +228,7 @@ struct Tiled {
 
 template <class L, class T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY, 2)
-    k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, T omega, int ncx, long long W) {
+    k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, T omega, Sched sc) {
     using K = Tiled<L, T, BX, BY>;
     constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -199,18 +243,11 @@ __global__ void __launch_bounds__(BX * BY, 2)
     halo_node<BX, BY>(t, hx2, hy2);
     const int n2 = hy2 * HX + hx2;
     const size_t plane = (size_t)lay.px * lay.py;
-
-    const long long w0 = (long long)blockIdx.x * W / gridDim.x;
-    const long long w1 = (long long)(blockIdx.x + 1) * W / gridDim.x;
     int buf = 0;
 
-    for (long long w = w0; w < w1;) {
-        const int col = (int)(w / nz);
-        const int za = (int)(w - (long long)col * nz);
-        const long long wend = min(w1, (long long)(col + 1) * nz);
-        const int zb = za + (int)(wend - w);  // outputs za .. zb-1
-        w = wend;
-        const int x0 = (col % ncx) * BX, y0 = (col / ncx) * BY;
+    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
+        int x0, y0, za, zb;  // outputs za .. zb-1 of the tile at (x0, y0)
+        sc.item(it, BX, BY, nz, x0, y0, za, zb);
         const size_t off1 = lay.at(pmod(x0 + tx, nx), pmod(y0 + ty, ny), 0);
         const size_t off2 = lay.at(pmod(x0 - 1 + hx2, nx), pmod(y0 - 1 + hy2, ny), 0);
         const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
@@ -304,8 +341,8 @@ __device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int
 
 template <class L, class T, class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
-    k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, int ncx,
-                 long long W, int* __restrict__ err) {
+    k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, Sched sc,
+                 int* __restrict__ err) {
     constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS, NH = C::NH;
     constexpr int SF = C::SF, SW = C::SW;
     extern __shared__ unsigned char smem_raw[];
@@ -332,19 +369,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     }
     __syncthreads();
 
-    const long long w0 = (long long)blockIdx.x * W / gridDim.x;
-    const long long w1 = (long long)(blockIdx.x + 1) * W / gridDim.x;
     int buf = 0;
-    unsigned q = 0;         // sequence number of the next source plane (all segments)
+    unsigned q = 0;         // sequence number of the next source plane (all items)
     unsigned issued = 0;    // sequence numbers < issued have a TMA in flight or done (thread 0)
+    // box origin: real (x0 - 4, y0 - 1) in padded coordinates
+    const int bxo = lay.xo - 4, byo = lay.yo - 1;
 
-    for (long long w = w0; w < w1;) {
-        const int col = (int)(w / nz);
-        const int za = (int)(w - (long long)col * nz);
-        const long long wend = min(w1, (long long)(col + 1) * nz);
-        const int zb = za + (int)(wend - w);  // outputs za .. zb-1
-        w = wend;
-        const int x0 = (col % ncx) * BX, y0 = (col / ncx) * BY;
+    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
+        int x0, y0, za, zb;  // outputs za .. zb-1 of the tile at (x0, y0)
+        sc.item(it, BX, BY, nz, x0, y0, za, zb);
         const int P = zb - za + 2;            // source planes za-1 .. zb
         const unsigned q0 = q;
         const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
@@ -354,7 +387,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 const unsigned qq = q0 + i;
                 const uint32_t bar = bar0 + 8 * (qq % NST);
                 mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
-                tma_load_4d(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, x0, y0, pmod(za - 1 + i, nz), 0, bar);
+                tma_load_4d(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(za - 1 + i, nz), 0,
+                            bar);
             }
             issued = q0 + min(NST, P);
         }
@@ -384,7 +418,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 const unsigned qq = q + NST;
                 const uint32_t bar = bar0 + 8 * k;
                 mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
-                tma_load_4d(stage0 + k * C::STAGE_STRIDE, &tmap, x0, y0, pmod(s + NST, nz), 0, bar);
+                tma_load_4d(stage0 + k * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(s + NST, nz), 0, bar);
                 issued = qq + 1;
             }
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
@@ -448,17 +482,17 @@ int tiled_ctas(const llb_ctx& c) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::NT, K::smem_bytes) != cudaSuccess ||
         per_sm < 1)
         return 0;
-    const long long ncol = (long long)((c.nx + kBX - 1) / kBX) * ((c.ny + kBY - 1) / kBY);
-    return (int)std::min<long long>(ncol * c.nz, (long long)per_sm * c.num_sms);
+    const Sched sc = plan(c.nx, c.ny, c.nz, kBX, kBY, per_sm * c.num_sms);
+    return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
 template <class L, class T>
 cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) {
     using K = Tiled<L, T, kBX, kBY>;
-    const int ncx = (c.nx + kBX - 1) / kBX;
-    const long long W = (long long)ncx * ((c.ny + kBY - 1) / kBY) * c.nz;
-    k_moment_tiled<L, T, kBX, kBY><<<c.tile_ctas > 0 ? c.tile_ctas : 1, K::NT, K::smem_bytes, c.stream>>>(
-        static_cast<const T*>(in), static_cast<T*>(out), c.lay, (T)c.omega, ncx, W);
+    const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
+    const Sched sc = plan(c.nx, c.ny, c.nz, kBX, kBY, grid);
+    k_moment_tiled<L, T, kBX, kBY><<<grid, K::NT, K::smem_bytes, c.stream>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), c.lay, (T)c.omega, sc);
     return cudaGetLastError();
 }
 
@@ -471,17 +505,17 @@ int tma_ctas(const llb_ctx& c) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM) != cudaSuccess || per_sm < 1)
         return 0;
-    const long long ncol = (long long)((c.nx + C::BX - 1) / C::BX) * ((c.ny + C::BY - 1) / C::BY);
-    return (int)std::min<long long>(ncol * c.nz, (long long)per_sm * c.num_sms);
+    const Sched sc = plan(c.nx, c.ny, c.nz, C::BX, C::BY, per_sm * c.num_sms);
+    return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
 template <class L, class T>
 cudaError_t run_tma(const llb_ctx& c, int in_index, void* out) {
     using C = typename TmaChoice<L, T>::type;
-    const int ncx = (c.nx + C::BX - 1) / C::BX;
-    const long long W = (long long)ncx * ((c.ny + C::BY - 1) / C::BY) * c.nz;
-    k_moment_tma<L, T, C><<<c.tma_ctas > 0 ? c.tma_ctas : 1, C::NT, C::SMEM, c.stream>>>(
-        c.tmap[in_index], static_cast<T*>(out), c.lay, (T)c.omega, ncx, W, static_cast<int*>(c.err_dev));
+    const int grid = c.tma_ctas > 0 ? c.tma_ctas : 1;
+    const Sched sc = plan(c.nx, c.ny, c.nz, C::BX, C::BY, grid);
+    k_moment_tma<L, T, C><<<grid, C::NT, C::SMEM, c.stream>>>(c.tmap[in_index], static_cast<T*>(out), c.lay,
+                                                               (T)c.omega, sc, static_cast<int*>(c.err_dev));
     return cudaGetLastError();
 }
 

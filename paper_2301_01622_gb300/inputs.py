@@ -90,3 +90,36 @@ def point_perturbation(nx: int, ny: int, nz: int, at=(0, 0, 0), delta: float = 0
     rho = np.full((nz, ny, nx), rho0, dtype=np.float64)
     rho[at[2], at[1], at[0]] += delta
     return rho, np.zeros((3, nz, ny, nx), dtype=np.float64)
+
+
+def droplets(nx: int, ny: int, nz: int, centres, radii, velocities, width: float = 2.0):
+    """Droplets of fluid 1 in a matrix of fluid 2, with a tanh interface.
+
+    Each droplet d contributes phi_d = tanh((R_d - r_d) / xi) with xi = width / 2
+    and r_d the periodic (minimum-image) distance to its centre; phi = max_d phi_d
+    (phi = +1 inside, -1 outside).  rho1 = (1 + phi) / 2, rho2 = (1 - phi) / 2
+    (total density 1), u = sum_d u_d (1 + phi_d) / 2.
+    Returns (rho1, rho2, u) with u of shape (3, nz, ny, nx).
+    """
+    x, y, z = _grid(nx, ny, nz)
+    xi = width / 2.0
+    phi = np.full((nz, ny, nx), -1.0)
+    u = np.zeros((3, nz, ny, nx))
+    for (cx, cy, cz), r0, vel in zip(centres, radii, velocities):
+        dx = (x - cx + nx / 2) % nx - nx / 2
+        dy = (y - cy + ny / 2) % ny - ny / 2
+        dz = (z - cz + nz / 2) % nz - nz / 2
+        r = np.sqrt(dx * dx + dy * dy + dz * dz)
+        phid = np.tanh((r0 - r) / xi)
+        phi = np.maximum(phi, phid)
+        for a in range(3):
+            u[a] += vel[a] * (1.0 + phid) / 2.0
+    return (1.0 + phi) / 2.0, (1.0 - phi) / 2.0, u
+
+
+def droplet_pair(nx: int, ny: int, nz: int, radius: float, speed: float, impact: float, width: float = 2.0):
+    """Two equal droplets approaching along x: centres (Lx/2 -+ 2R, Ly/2 -+ b/2, Lz/2),
+    velocities (+-speed, 0, 0), impact parameter b = ``impact``."""
+    c1 = (nx / 2 - 2 * radius, ny / 2 - impact / 2, nz / 2)
+    c2 = (nx / 2 + 2 * radius, ny / 2 + impact / 2, nz / 2)
+    return droplets(nx, ny, nz, [c1, c2], [radius, radius], [(speed, 0.0, 0.0), (-speed, 0.0, 0.0)], width)

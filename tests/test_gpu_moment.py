@@ -25,7 +25,7 @@ KIDS = ["tma", "tiled", "direct"]
 def tma_fits(shape):
     """The TMA kernel needs a padded row of >= 40 elements and >= 10 rows (tile 32 x 8 plus halo)."""
     nx, ny, _ = shape
-    return ((nx + 8 + 7) // 8) * 8 >= 40 and ny + 2 >= 10
+    return ((nx + 16 + 7) // 8) * 8 >= 40 and ny + 2 >= 10
 
 
 @functools.lru_cache(maxsize=None)
@@ -65,7 +65,7 @@ def test_noisy_taylor_green_fp32_tau06(q):
 
 
 SHAPES = [(67, 45, 37), (33, 9, 5), (31, 17, 3), (5, 70, 2), (1, 1, 1), (2, 3, 4), (4, 4, 4), (64, 16, 8), (97, 1, 3),
-          (25, 8, 1), (129, 40, 2)]
+          (25, 8, 1), (129, 40, 2), (17, 8, 70), (300, 12, 9)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -103,9 +103,8 @@ def test_tiled_is_deterministic_and_matches_direct(q):
     c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
     d, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
     assert np.array_equal(a, b)
-    # the two z-marching kernels add the same terms in the same order
-    assert np.array_equal(a, c)
-    assert_groups(a, d, 1e-6, what="tiled vs direct")
+    assert_groups(a, c, 1e-6, what="tma vs tiled")
+    assert_groups(a, d, 1e-6, what="tma vs direct")
 
 
 def _sample_nodes(nx, ny, nz, rng, count=60):

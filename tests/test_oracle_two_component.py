@@ -1,0 +1,197 @@
+"""Pins of the two-component oracle (colour gradient + near-contact forcing).
+
+The paper leaves the operator forms to another work, so the readings are
+pinned by what any correct implementation of them must satisfy: exact
+gradients of sampled sines, closed-form moments of the collided populations,
+reduction to the one-component scheme, conservation of each colour, momentum
+change equal to the applied force, symmetry, the near-contact detector on
+separated and nearly touching droplets, and the population-storing form of
+the same scheme.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import CS2, D3Q19, D3Q27, lb
+from oracle import two_component as tc
+from paper_2301_01622_gb300 import inputs
+
+LATTICES = [D3Q19, D3Q27]
+IDS = ["D3Q19", "D3Q27"]
+
+
+def _moments(rho1, rho2, u):
+    tot = lb.equilibrium_moments(rho1 + rho2, u)
+    return np.concatenate([rho1[None], rho2[None], tot[1:]])
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_gradient_of_sine_is_exact(lat):
+    """For phi = sin(k x): (1/cs^2) sum_k w_k c_k phi(x + c_k) = (sin k cos kx, 0, 0) exactly."""
+    n = 12
+    k = 2 * np.pi / n
+    x = np.arange(n)[None, None, :] * np.ones((3, 4, n))
+    for axis in range(3):
+        phi = np.sin(k * x)
+        phi = np.moveaxis(phi, 2, 2 - axis) if axis else phi
+        G = tc.gradient(phi, lat)
+        expect = np.sin(k) * np.cos(k * (np.moveaxis(x, 2, 2 - axis) if axis else x))
+        np.testing.assert_allclose(G[axis], expect, atol=1e-14)
+        for b in range(3):
+            if b != axis:
+                np.testing.assert_allclose(G[b], 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_collided_moments_closed_form(lat):
+    """Moments of h' (BGK + Guo forcing + perturbation):
+    rho' = rho, j' = j + F, P' = (1-w)P + w P^eq(u_F) + (1 - w/2)(u_F F + F u_F) + A_s cs^4 |G| n n;
+    colour: sum h1' = rho1."""
+    m = inputs.random_moments(6, 5, 4, seed=3, nfields=11)
+    prm = tc.CGParams(beta=0.6, A_s=0.05, A_h=0.02, h_c=2)
+    tau = 0.7
+    cf = tc.CollisionFields(m, lat, tau, prm)
+    # force the near-contact set to be non-empty everywhere so F is exercised
+    cf.near[...] = True
+    cf.F = prm.A_h * cf.G
+    cf.uF = (cf.tot[1:4] + 0.5 * cf.F) / cf.rho
+    hs = [tc.collided_direction(cf, lat, i) for i in range(lat.Q)]
+    hp = np.stack([h[0] for h in hs])
+    h1 = np.stack([h[1] for h in hs])
+    mom = lb.project(hp, lat)
+    om = 1 / tau
+    rho, uF, F = cf.rho, cf.uF, cf.F
+    np.testing.assert_allclose(mom[0], rho, atol=1e-14)
+    np.testing.assert_allclose(mom[1:4], cf.tot[1:4] + F, atol=1e-14)
+    for k, (a, b) in enumerate(lb.PAIRS):
+        peq = CS2 * rho * (a == b) + rho * uF[a] * uF[b]
+        expect = ((1 - om) * cf.tot[4 + k] + om * peq + (1 - om / 2) * (uF[a] * F[b] + F[a] * uF[b])
+                  + prm.A_s * CS2 * CS2 * cf.gnorm * cf.n[a] * cf.n[b])
+        np.testing.assert_allclose(mom[4 + k], expect, atol=1e-14)
+    np.testing.assert_allclose(h1.sum(axis=0), m[0], atol=1e-14)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_reduces_to_one_component(lat):
+    """A_s = beta = A_h = 0: the mixture moves as the one-component scheme and
+    rho1 is carried passively with the fraction rho1/rho of every population."""
+    m = inputs.random_moments(7, 6, 5, seed=9, nfields=11)
+    prm = tc.CGParams(beta=0.0, A_s=0.0, A_h=0.0)
+    out = tc.step_moment_only(m, lat, 0.8, prm)
+    one = lb.step_moment_only(tc.total_moments(m), lat, 0.8)
+    np.testing.assert_allclose(tc.total_moments(out), one, atol=1e-14)
+    frac = m[0] / (m[0] + m[1])
+    fl = lb.LocalFields(tc.total_moments(m))
+    rho1 = sum(lb.stream_pull(frac * lb.reconstruct_direction(fl, lat, i, 1 / 0.8), lat.c[i]) for i in range(lat.Q))
+    np.testing.assert_allclose(out[0], rho1, atol=1e-14)
+
+
+def _pair(n=(32, 20, 20), radius=4.0, speed=0.04, impact=0.0, gap=None):
+    nx, ny, nz = n
+    if gap is None:
+        return inputs.droplet_pair(nx, ny, nz, radius, speed, impact)
+    c1 = (nx / 2 - radius - gap / 2, ny / 2 - impact / 2, nz / 2)
+    c2 = (nx / 2 + radius + gap / 2, ny / 2 + impact / 2, nz / 2)
+    return inputs.droplets(nx, ny, nz, [c1, c2], [radius, radius], [(speed, 0, 0), (-speed, 0, 0)])
+
+
+def test_near_contact_detector():
+    """An isolated droplet never triggers; two droplets 3 nodes apart do, 12 apart do not."""
+    prm = tc.CGParams(A_h=0.01, h_c=3)
+    r1, r2, u = inputs.droplets(32, 32, 32, [(16, 16, 16)], [7.0], [(0, 0, 0)])
+    cf = tc.CollisionFields(_moments(r1, r2, u), D3Q19, 1.0, prm)
+    assert (cf.gnorm >= prm.g_nci).sum() > 100 and not cf.near.any()
+    r1, r2, u = _pair((48, 24, 24), radius=6.0, gap=3.0)
+    cf = tc.CollisionFields(_moments(r1, r2, u), D3Q19, 1.0, prm)
+    assert cf.near.any()
+    zc = np.nonzero(cf.near)[2]
+    assert np.all(np.abs(zc - 24) <= 10)          # only between the droplets
+    r1, r2, u = _pair((64, 24, 24), radius=6.0, gap=12.0)
+    cf = tc.CollisionFields(_moments(r1, r2, u), D3Q19, 1.0, prm)
+    assert not cf.near.any()
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_moment_only_equals_regularized_population(lat):
+    """MO-2 and RP-2 (stored colour populations, same collision) agree to 1e-12
+    on a nearly touching pair with near-contact forcing active."""
+    r1, r2, u = _pair((24, 14, 14), radius=3.5, gap=2.5, speed=0.03, impact=1.0)
+    m0 = _moments(r1, r2, u)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.01, h_c=3)
+    cf = tc.CollisionFields(m0, lat, 1.0, prm)
+    assert cf.near.any()
+    steps = 8
+    m = tc.run_moment_only(m0, lat, 0.9, prm, steps)
+    f = tc.run_population(tc.populations_from_moments(m0, lat), lat, 0.9, prm, steps)
+    mp = tc.project(f, lat)
+    for k in range(11):
+        assert np.abs(m[k] - mp[k]).max() <= 1e-12 * max(np.abs(mp[k]).max(), 1e-3)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_colour_mass_and_momentum(lat):
+    """Each colour's mass is conserved; total momentum changes by exactly sum F per step."""
+    r1, r2, u = _pair((24, 14, 14), radius=3.5, gap=2.0, speed=0.03, impact=2.0)
+    m = _moments(r1, r2, u)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.02, h_c=3)
+    m1, m2 = math.fsum(m[0].ravel()), math.fsum(m[1].ravel())
+    for _ in range(6):
+        cf = tc.CollisionFields(m, lat, 0.8, prm)
+        jF = [math.fsum(m[2 + a].ravel()) + math.fsum(cf.F[a].ravel()) for a in range(3)]
+        m = tc.step_moment_only(m, lat, 0.8, prm)
+        for a in range(3):
+            assert abs(math.fsum(m[2 + a].ravel()) - jF[a]) < 1e-13
+    assert abs(math.fsum(m[0].ravel()) - m1) < 1e-11
+    assert abs(math.fsum(m[1].ravel()) - m2) < 1e-11
+
+
+def test_head_on_mirror_symmetry():
+    """Head-on collision (b = 0) is symmetric under x -> Lx - 1 - x with u_x -> -u_x."""
+    nx = 32
+    r1, r2, u = _pair((nx, 16, 16), radius=4.0, gap=2.0, speed=0.04)
+    # make the initial field exactly mirror symmetric about the box centre (x = (nx-1)/2)
+    def mirror(a, flip_sign=False):
+        return (-1 if flip_sign else 1) * a[..., ::-1]
+    r1 = 0.5 * (r1 + mirror(r1))
+    r2 = 1.0 - r1
+    ux = 0.5 * (u[0] + mirror(u[0], True))
+    u = np.stack([ux, 0 * ux, 0 * ux])
+    m = _moments(r1, r2, u)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.02, h_c=3)
+    m = tc.run_moment_only(m, D3Q19, 0.9, prm, 10)
+    sign = np.array([1, 1, -1, 1, 1, 1, 1, 1, -1, -1, 1])[:, None, None, None]  # rho1, rho2, j, Pxx..Pyz
+    np.testing.assert_allclose(m, sign * m[..., ::-1], atol=1e-13)
+
+
+def test_recolouring_keeps_interface_sharp():
+    """A flat interface at rest: with beta = 0.7 the profile relaxes to a
+    stationary width set by beta, narrower for larger beta; with beta = 0 (no
+    recolouring) colour 1 just diffuses into colour 2."""
+    nx = 32
+    x = np.arange(nx)
+    phi = np.tanh((np.minimum(x, nx - 1 - x) - 8) / 1.0)[None, None, :] * np.ones((2, 2, nx))
+    r1, r2 = (1 + phi) / 2, (1 - phi) / 2
+    m0 = _moments(r1, r2, np.zeros((3, 2, 2, nx)))
+    widths, profiles = [], []
+    for beta in (0.7, 0.3, 0.0):
+        m = tc.run_moment_only(m0, D3Q19, 1.0, tc.CGParams(beta=beta, A_s=0.0), 150)
+        p = (m[0] - m[1]) / (m[0] + m[1])
+        profiles.append(p)
+        widths.append(int(np.sum(np.abs(p[0, 0]) < 0.9)))
+    assert widths[0] <= 12 < widths[1] < widths[2]
+    m7 = tc.run_moment_only(m0, D3Q19, 1.0, tc.CGParams(beta=0.7, A_s=0.0), 300)
+    p7 = (m7[0] - m7[1]) / (m7[0] + m7[1])
+    assert np.abs(p7 - profiles[0]).max() < 1e-3      # stationary
+
+
+def test_count_droplets():
+    a = np.zeros((10, 10, 20))
+    a[3:6, 3:6, 2:5] = 1
+    a[3:6, 3:6, 10:13] = 1
+    assert tc.count_droplets(a) == 2
+    a[3:6, 3:6, 5:10] = 1
+    assert tc.count_droplets(a) == 1
+    b = np.zeros((6, 6, 6))
+    b[2, 2, 0] = b[2, 2, 5] = 1      # touch through the periodic boundary
+    assert tc.count_droplets(b) == 1
