@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the D3Q27 and population lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tma", "tiled", "direct"],
                     help="moment-only kernel (auto = the library's choice)")
+    ap.add_argument("--variant", type=int, default=0, help="TMA kernel variant (tuning)")
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="lattice of the main line")
     return ap.parse_args()
 
 
@@ -189,13 +191,13 @@ def ncu_traffic(key: str):
 
 
 KERNEL_CODE = {"auto": 0, "direct": 1, "tiled": 2, "tma": 3}
-_KERNEL = ["auto"]
+_KERNEL = ["auto", 0]
 
 
 def make_ctx(llb, lattice, scheme, stream, storage=None):
     kern = KERNEL_CODE[_KERNEL[0]] if scheme == llb.LLB_SCHEME_MOMENT else 0
     p = llb.llb_params_default(storage=llb.LLB_F32 if storage is None else storage, scheme=scheme,
-                               stream=stream, kernel=kern)
+                               stream=stream, kernel=kern, variant=_KERNEL[1])
     return llb.llb_create(NX, NY, NZ, lattice, TAU, p)
 
 
@@ -249,7 +251,7 @@ def gpu_arm(args, rank, world, local):
                 "bytes_per_node": fp.stream_bytes_per_node, "kernel": kernel, "clocks": clocks,
                 "launch_ms": ms / args.steps}
 
-    main = run(LATTICE, llb.LLB_SCHEME_MOMENT, ClockSampler(local))
+    main = run(args.lattice, llb.LLB_SCHEME_MOMENT, ClockSampler(local))
     extra = {}
     if not args.no_extra:
         extra["population_d3q19"] = run(19, llb.LLB_SCHEME_POPULATION)
@@ -389,6 +391,7 @@ def reference_arm(args, rank):
 def main():
     args = parse()
     _KERNEL[0] = args.kernel
+    _KERNEL[1] = args.variant
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         line = reference_arm(args, rank)

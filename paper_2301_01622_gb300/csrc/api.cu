@@ -70,6 +70,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
         p.kernel != LLB_KERNEL_TMA) {
         *why = "unknown kernel"; return LLB_EINVAL;
     }
+    if (p.variant < 0 || p.variant > 4) { *why = "variant must be in 0..4"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
         *why = "two-component model not available in this build";
         return LLB_EINVAL;
@@ -84,6 +85,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     c->storage = p.storage;
     c->scheme = p.scheme;
     c->kernel = p.kernel;
+    c->variant = p.variant;
     c->params = p;
     c->N = (size_t)nx * ny * nz;
     c->nf = fields_of(*c);

@@ -18,6 +18,7 @@ struct llb_ctx {
     int storage = LLB_F32;   // element type of the device state
     int scheme = LLB_SCHEME_MOMENT;
     int kernel = LLB_KERNEL_AUTO;  // resolved kernel (never AUTO after create)
+    int variant = 0;               // tile/pipeline variant of the TMA kernel
     double tau = 1.0, omega = 1.0;
     llb_params params{};
     cudaStream_t stream = nullptr;

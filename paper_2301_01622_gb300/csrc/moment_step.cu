@@ -155,31 +155,139 @@ __global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in,
 // ---------------------------------------------------------------------------
 // Shared pieces of the two z-marching kernels.
 
-// Publish the column-crossing populations of one collided node into G[k][n].
-template <class L, class T, int HN>
+// Slot of direction (cx, cy, cz) among the column-crossing directions
+// ((cx, cy) != (0, 0)), enumerated over cz, cy, cx in {-1, 0, 1}.
+template <class L>
+__host__ __device__ constexpr int kslot(int cx, int cy, int cz) {
+    int k = 0;
+    for (int z = -1; z <= 1; ++z)
+        for (int y = -1; y <= 1; ++y)
+            for (int x = -1; x <= 1; ++x) {
+                if (!L::has(x, y, z) || (x == 0 && y == 0)) continue;
+                if (x == cx && y == cy && z == cz) return k;
+                ++k;
+            }
+    return -1;
+}
+
+// Which crossing directions a node of the staged tile publishes: all of them
+// for a tile node, only those pointing into the tile for a halo node (a halo
+// node above the tile feeds its outputs only along c_y = +1, and so on).
+constexpr int kAny = 2;
+
+template <int RX, int RY>
+__host__ __device__ constexpr bool wanted(int cx, int cy) {
+    return (RX == kAny || cx == RX) && (RY == kAny || cy == RY);
+}
+
+// Publish the crossing populations of one collided node into G[k][n].
+// Directions come in opposite pairs (c, -c) sharing the even part of Eq.
+// (coll2): g'_{+-c} = w (q +- l) with q = d - 1.5 tr A' + 4.5 c c : A',
+// l = 3 c.j.
+template <class L, class T, int HN, int RX = kAny, int RY = kAny>
 __device__ __forceinline__ void publish(T* __restrict__ G, int n, const Mom<T>& c) {
     const T s0 = g_shared(c);
-    int k = 0;
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
         for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0)) continue;
-                G[k * HN + n] = g_dir<L, T>(c, s0, cx, cy, cz);
-                ++k;
+                // visit each pair once, from its member with the first non-zero component > 0
+                const bool lead = cx > 0 || (cx == 0 && (cy > 0 || (cy == 0 && cz > 0)));
+                if (!lead || !L::has(cx, cy, cz) || (cx == 0 && cy == 0)) continue;
+                const bool wp = wanted<RX, RY>(cx, cy), wm = wanted<RX, RY>(-cx, -cy);
+                if (!wp && !wm) continue;
+                T q = s0;
+                if (cx) q += T(4.5) * c.axx;
+                if (cy) q += T(4.5) * c.ayy;
+                if (cz) q += T(4.5) * c.azz;
+                if (cx * cy) q += T(9 * cx * cy) * c.axy;
+                if (cx * cz) q += T(9 * cx * cz) * c.axz;
+                if (cy * cz) q += T(9 * cy * cz) * c.ayz;
+                T l = T(0);
+                if (cx) l += T(3 * cx) * c.jx;
+                if (cy) l += T(3 * cy) * c.jy;
+                if (cz) l += T(3 * cz) * c.jz;
+                const T w = T(L::w(cx, cy, cz));
+                const T wq = w * q, wl = w * l;
+                if (wp) G[kslot<L>(cx, cy, cz) * HN + n] = wq + wl;
+                if (wm) G[kslot<L>(-cx, -cy, -cz) * HN + n] = wq - wl;
             }
+}
+
+// Populations g'_i of the own column (c_x = c_y = 0): directions -z, 0, +z.
+template <class L, class T>
+__device__ __forceinline__ void own_column(const Mom<T>& c, T& g_m, T& g_0, T& g_p) {
+    const T s0 = g_shared(c);
+    const T wz = T(L::w(0, 0, 1));
+    const T wq = wz * (s0 + T(4.5) * c.azz), wl = wz * (T(3) * c.jz);
+    g_p = wq + wl;
+    g_m = wq - wl;
+    g_0 = T(L::w(0, 0, 0)) * s0;
+}
+
+// Add the populations that node n1 pulls from source plane s with c_z = CZ
+// into the accumulator of plane s + CZ.  Opposite directions in x (and y)
+// are combined first (sum and difference), so each moment gets one add per
+// pair instead of one per direction.
+template <class L, class T, int CZ>
+__device__ __forceinline__ void add_plane(const T* __restrict__ g, T g_own, Acc<T>& A) {
+    T sum = g_own, jx = T(0), jy = T(0), sxx = T(0), syy = T(0), sxy = T(0);
+    if (L::has(1, 0, CZ)) {
+        const T a = g[kslot<L>(1, 0, CZ)], b = g[kslot<L>(-1, 0, CZ)];
+        const T s = a + b;
+        sum += s;
+        sxx += s;
+        jx += a - b;
+    }
+    if (L::has(0, 1, CZ)) {
+        const T a = g[kslot<L>(0, 1, CZ)], b = g[kslot<L>(0, -1, CZ)];
+        const T s = a + b;
+        sum += s;
+        syy += s;
+        jy += a - b;
+    }
+    if (L::has(1, 1, CZ)) {
+        const T pp = g[kslot<L>(1, 1, CZ)], mm = g[kslot<L>(-1, -1, CZ)];
+        const T pm = g[kslot<L>(1, -1, CZ)], mp = g[kslot<L>(-1, 1, CZ)];
+        const T a = pp + mm, b = pm + mp, c = pp - mm, e = pm - mp;
+        const T s = a + b;
+        sum += s;
+        sxx += s;
+        syy += s;
+        sxy += a - b;
+        jx += c + e;
+        jy += c - e;
+    }
+    A.d += sum;
+    A.jx += jx;
+    A.jy += jy;
+    A.sxx += sxx;
+    A.syy += syy;
+    A.sxy += sxy;
+    if (CZ != 0) {
+        A.szz += sum;
+        if (CZ > 0) {
+            A.jz += sum;
+            A.sxz += jx;
+            A.syz += jy;
+        } else {
+            A.jz -= sum;
+            A.sxz -= jx;
+            A.syz -= jy;
+        }
+    }
 }
 
 // Pull the crossing populations of output node n1 from G and add them to the
-// accumulators of planes s-1 (X), s (Y), s+1 (Z); the own-column populations
-// (c_x = c_y = 0) come from registers.
+// accumulators of planes s-1 (X), s (Y), s+1 (Z, started here); the
+// own-column populations come from registers.
 template <class L, class T, int HN, int HX>
 __device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T g_0, T g_p, Acc<T>& X, Acc<T>& Y,
                                        Acc<T>& Z) {
-    Z.zero();
-    int k = 0;
+    constexpr int NS = n_xy_shifted<L>();
+    T g[NS];
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
@@ -187,29 +295,49 @@ __device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0)) continue;
-                const T g = G[k * HN + n1 - cy * HX - cx];
-                if (cz < 0) X.add(g, cx, cy, cz);
-                else if (cz == 0) Y.add(g, cx, cy, cz);
-                else Z.add(g, cx, cy, cz);
-                ++k;
+                const int k = kslot<L>(cx, cy, cz);
+                g[k] = G[k * HN + n1 - cy * HX - cx];
             }
-    X.add(g_m, 0, 0, -1);
-    Y.add(g_0, 0, 0, 0);
-    Z.add(g_p, 0, 0, 1);
+    Z.zero();
+    add_plane<L, T, -1>(g, g_m, X);
+    add_plane<L, T, 0>(g, g_0, Y);
+    add_plane<L, T, 1>(g, g_p, Z);
 }
 
-// Halo node handled by thread t < NH: top row, bottom row, then side columns.
+// Halo node handled by thread t < NH and its role.  Warp-uniform where the
+// tile width allows: threads [0, BX) take the row above the tile, [BX, 2 BX)
+// the row below, then the left and right columns and the four corners.
+enum HaloRole { kNone, kTop, kBottom, kLeft, kRight, kTL, kTR, kBL, kBR };
+
 template <int BX, int BY>
-__device__ __forceinline__ void halo_node(int t, int& hx, int& hy) {
-    constexpr int HX = BX + 2;
-    if (t < HX) {
-        hx = t; hy = 0;
-    } else if (t < 2 * HX) {
-        hx = t - HX; hy = BY + 1;
-    } else {
-        const int k = t - 2 * HX;
-        hy = 1 + (k >> 1);
-        hx = (k & 1) ? (BX + 1) : 0;
+__device__ __forceinline__ int halo_node(int t, int& hx, int& hy) {
+    if (t < BX) { hx = t + 1; hy = 0; return kTop; }
+    if (t < 2 * BX) { hx = t - BX + 1; hy = BY + 1; return kBottom; }
+    const int s = t - 2 * BX;
+    if (s < BY) { hx = 0; hy = s + 1; return kLeft; }
+    if (s < 2 * BY) { hx = BX + 1; hy = s - BY + 1; return kRight; }
+    switch (s - 2 * BY) {
+        case 0: hx = 0; hy = 0; return kTL;
+        case 1: hx = BX + 1; hy = 0; return kTR;
+        case 2: hx = 0; hy = BY + 1; return kBL;
+        case 3: hx = BX + 1; hy = BY + 1; return kBR;
+        default: hx = 0; hy = 0; return kNone;
+    }
+}
+
+// Publish a collided halo node: only the directions its role feeds.
+template <class L, class T, int HN>
+__device__ __forceinline__ void publish_halo(T* __restrict__ G, int n, int role, const Mom<T>& c) {
+    switch (role) {
+        case kTop: publish<L, T, HN, kAny, 1>(G, n, c); break;
+        case kBottom: publish<L, T, HN, kAny, -1>(G, n, c); break;
+        case kLeft: publish<L, T, HN, 1, kAny>(G, n, c); break;
+        case kRight: publish<L, T, HN, -1, kAny>(G, n, c); break;
+        case kTL: publish<L, T, HN, 1, 1>(G, n, c); break;
+        case kTR: publish<L, T, HN, -1, 1>(G, n, c); break;
+        case kBL: publish<L, T, HN, 1, -1>(G, n, c); break;
+        case kBR: publish<L, T, HN, -1, -1>(G, n, c); break;
+        default: break;
     }
 }
 
@@ -238,9 +366,9 @@ __global__ void __launch_bounds__(BX * BY, 2)
     const int t = threadIdx.x;
     const int tx = t % BX, ty = t / BX;
     const int n1 = (ty + 1) * HX + (tx + 1);
-    const bool has2 = t < NH;
     int hx2, hy2;
-    halo_node<BX, BY>(t, hx2, hy2);
+    const int role2 = halo_node<BX, BY>(t, hx2, hy2);
+    const bool has2 = role2 != kNone;
     const int n2 = hy2 * HX + hx2;
     const size_t plane = (size_t)lay.px * lay.py;
     int buf = 0;
@@ -271,11 +399,9 @@ __global__ void __launch_bounds__(BX * BY, 2)
             }
             const Mom<T> c1 = collide(m1, omega);
             publish<L, T, HN>(G, n1, c1);
-            const T s01 = g_shared(c1);
-            const T g_m = g_dir<L, T>(c1, s01, 0, 0, -1);
-            const T g_0 = g_dir<L, T>(c1, s01, 0, 0, 0);
-            const T g_p = g_dir<L, T>(c1, s01, 0, 0, 1);
-            if (has2) publish<L, T, HN>(G, n2, collide(m2, omega));
+            T g_m, g_0, g_p;
+            own_column<L, T>(c1, g_m, g_0, g_p);
+            if (has2) publish_halo<L, T, HN>(G, n2, role2, collide(m2, omega));
             __syncthreads();
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
             if (s - 1 >= za && store_ok) store_node(out, lay, x0 + tx, y0 + ty, s - 1, X.finish());
@@ -301,7 +427,7 @@ __global__ void __launch_bounds__(BX * BY, 2)
 
 // ---------------------------------------------------------------------------
 // TMA-staged z-marching kernel.
-template <class L, class T, int BX_, int BY_, int NST_>
+template <class L, class T, int BX_, int BY_, int NST_, int MINB_>
 struct TmaCfg {
     static constexpr int BX = BX_, BY = BY_, NST = NST_;
     static constexpr int NT = BX * BY;
@@ -316,7 +442,7 @@ struct TmaCfg {
     static constexpr int G_BYTES = 2 * NS * HN * (int)sizeof(T);
     static constexpr int BAR_OFF = (G_OFF + G_BYTES + 7) / 8 * 8;
     static constexpr int SMEM = BAR_OFF + 8 * NST + 1024;  // + slack to align the base to 1 KB
-    static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;    // CTAs per SM the register budget targets
+    static constexpr int MINB = MINB_;                      // CTAs per SM the register budget targets
     static_assert(NH <= NT, "halo must fit one node per thread");
     static_assert(SW * (int)sizeof(T) % 16 == 0, "TMA box row must be a multiple of 16 bytes");
     static_assert(SW <= 256 && SR <= 256, "TMA box dimension limit");
@@ -356,9 +482,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int t = threadIdx.x;
     const int tx = t % BX, ty = t / BX;
     const int n1 = (ty + 1) * HX + (tx + 1);
-    const bool has2 = t < NH;
     int hx2, hy2;
-    halo_node<BX, BY>(t, hx2, hy2);
+    const int role2 = halo_node<BX, BY>(t, hx2, hy2);
+    const bool has2 = role2 != kNone;
     const int n2 = hy2 * HX + hx2;
 
     if (t == 0) {
@@ -405,11 +531,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             if (ok) {
                 const Mom<T> c1 = collide(stage_mom<T, SF, SW>(S, tx + 1, ty + 1), omega);
                 publish<L, T, HN>(G, n1, c1);
-                const T s01 = g_shared(c1);
-                g_m = g_dir<L, T>(c1, s01, 0, 0, -1);
-                g_0 = g_dir<L, T>(c1, s01, 0, 0, 0);
-                g_p = g_dir<L, T>(c1, s01, 0, 0, 1);
-                if (has2) publish<L, T, HN>(G, n2, collide(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
+                own_column<L, T>(c1, g_m, g_0, g_p);
+                if (has2) publish_halo<L, T, HN>(G, n2, role2, collide(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
             }
             if (__syncthreads_or(!ok)) return false;
             // every thread is done with stage k: refill it with plane s + NST
@@ -458,11 +581,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
 constexpr int kBX = 32, kBY = 8;
 
-template <class L, class T>
-struct TmaChoice {
-    // FP32: 4 stages of 16 KB; FP64 stages are twice as large, so 2.
-    using type = TmaCfg<L, T, 32, 8, (sizeof(T) == 4 ? 4 : 2)>;
-};
+// TMA kernel variants (tile BX x BY, ring depth, CTAs per SM).  Variant 0 is
+// the default; the others exist for tuning sweeps (llb_params.variant).
+template <class L, class T, int V>
+struct TmaVariant;
+template <class L> struct TmaVariant<L, float, 0> { using type = TmaCfg<L, float, 32, 8, 4, 2>; };
+template <class L> struct TmaVariant<L, float, 1> { using type = TmaCfg<L, float, 32, 8, 3, 3>; };
+template <class L> struct TmaVariant<L, float, 2> { using type = TmaCfg<L, float, 32, 16, 3, 1>; };
+template <class L> struct TmaVariant<L, float, 3> { using type = TmaCfg<L, float, 64, 8, 3, 1>; };
+template <class L> struct TmaVariant<L, float, 4> { using type = TmaCfg<L, float, 64, 4, 4, 2>; };
+template <class L, int V> struct TmaVariant<L, double, V> { using type = TmaCfg<L, double, 32, 8, 2, 1>; };
+constexpr int kTmaVariants = 5;
 
 template <class L, class T>
 cudaError_t run_direct(const llb_ctx& c, const void* in, void* out) {
@@ -496,9 +625,8 @@ cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) {
     return cudaGetLastError();
 }
 
-template <class L, class T>
-int tma_ctas(const llb_ctx& c) {
-    using C = typename TmaChoice<L, T>::type;
+template <class L, class T, class C>
+int tma_ctas_c(const llb_ctx& c) {
     if (!c.lay.ghosts || c.lay.px < C::SW || c.lay.py < C::SR) return 0;
     auto kern = k_moment_tma<L, T, C>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return 0;
@@ -509,9 +637,8 @@ int tma_ctas(const llb_ctx& c) {
     return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
-template <class L, class T>
-cudaError_t run_tma(const llb_ctx& c, int in_index, void* out) {
-    using C = typename TmaChoice<L, T>::type;
+template <class L, class T, class C>
+cudaError_t run_tma_c(const llb_ctx& c, int in_index, void* out) {
     const int grid = c.tma_ctas > 0 ? c.tma_ctas : 1;
     const Sched sc = plan(c.nx, c.ny, c.nz, C::BX, C::BY, grid);
     k_moment_tma<L, T, C><<<grid, C::NT, C::SMEM, c.stream>>>(c.tmap[in_index], static_cast<T*>(out), c.lay,
@@ -519,9 +646,8 @@ cudaError_t run_tma(const llb_ctx& c, int in_index, void* out) {
     return cudaGetLastError();
 }
 
-template <class L, class T>
-bool tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
-    using C = typename TmaChoice<L, T>::type;
+template <class L, class T, class C>
+bool tma_encode_c(const llb_ctx& c, void* buf, CUtensorMap* out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -543,6 +669,22 @@ bool tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
+
+#define LLB_TMA_VARIANT(fn, ...)                                                                  \
+    switch (c.variant) {                                                                          \
+        case 1: return fn<L, T, typename TmaVariant<L, T, 1>::type>(__VA_ARGS__);                 \
+        case 2: return fn<L, T, typename TmaVariant<L, T, 2>::type>(__VA_ARGS__);                 \
+        case 3: return fn<L, T, typename TmaVariant<L, T, 3>::type>(__VA_ARGS__);                 \
+        case 4: return fn<L, T, typename TmaVariant<L, T, 4>::type>(__VA_ARGS__);                 \
+        default: return fn<L, T, typename TmaVariant<L, T, 0>::type>(__VA_ARGS__);                \
+    }
+
+template <class L, class T>
+int tma_ctas(const llb_ctx& c) { LLB_TMA_VARIANT(tma_ctas_c, c) }
+template <class L, class T>
+cudaError_t run_tma(const llb_ctx& c, int in_index, void* out) { LLB_TMA_VARIANT(run_tma_c, c, in_index, out) }
+template <class L, class T>
+bool tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) { LLB_TMA_VARIANT(tma_encode_c, c, buf, out) }
 
 }  // namespace
 

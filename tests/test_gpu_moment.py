@@ -87,6 +87,20 @@ def test_ragged_shapes_random_moments_fp64(shape, q, kernel):
     assert_groups(got, ref, 1e-12, what=f"{shape} D3Q{q}")
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("q", [19, 27])
+def test_tma_variants_match_oracle(variant, q):
+    """Every tuning variant of the TMA kernel (tile shape, ring depth, CTAs/SM)
+    computes the same step: ragged multi-tile box, FP32, 1e-5 after 20 steps."""
+    shape = (133, 37, 29)
+    rho, u = inputs.taylor_green_3d(*shape, u0=0.05, noise=1e-3, seed=7)
+    ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
+    got, used = run_gpu(shape, q, 0.7, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA,
+                        variant=variant)
+    assert used == llb.LLB_KERNEL_TMA
+    assert_groups(got, ref, 1e-5, what=f"variant {variant}")
+
+
 @pytest.mark.parametrize("q", [19, 27])
 def test_zero_steps_round_trip(q):
     m0 = inputs.random_moments(7, 5, 3, seed=3)
