@@ -182,6 +182,31 @@ LLB_API int llb_get_moments_device(llb_ctx* ctx, void* dev_out, int dtype);
  * momentum conservation).  Synchronises the stream. */
 LLB_API int llb_diagnostics(llb_ctx* ctx, llb_diag* out);
 
+/* Diagnostics of canonical one-component moments (rho, j, P; layout above)
+ * that are already in DEVICE memory, with the same FP64 sums as
+ * llb_diagnostics, for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment convenience.
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph (an allocation there invalidates the capture), frameworks that own
+ * the device allocator, real-time loops that forbid allocation on the hot
+ * path, and embedders with a fixed memory budget.  This call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
+ * scratch is a fixed 256 KB array in device memory that every GPU which
+ * loads the library holds until the process exits.
+ *
+ * dev_m: nx*ny*nz*10 elements of type dtype (LLB_F32 or LLB_F64), caller-owned.
+ * stream: cudaStream_t (NULL = legacy default stream).  host_out: caller-owned
+ * host struct, filled before the call returns (the call synchronises the
+ * stream).  Limits: nx*ny*nz <= 67,108,864 nodes, else LLB_EINVAL and nothing
+ * runs.  Every call shares the one scratch array: calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and must be ordered by
+ * the caller.  The first call on a device looks up the scratch address with
+ * that device current; make that first call before any stream capture.
+ * Returns LLB_OK, LLB_EINVAL or LLB_ECUDA. */
+LLB_API int llb_diagnostics_noalloc(const void* dev_m, int dtype, int nx, int ny, int nz, void* stream,
+                                    llb_diag* host_out);
+
 /* Wait for all work of the context. */
 LLB_API int llb_synchronize(llb_ctx* ctx);
 

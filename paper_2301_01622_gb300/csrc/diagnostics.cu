@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <mutex>
 
 #include "internal.h"
 #include "lattice.cuh"
@@ -147,3 +148,116 @@ cudaError_t launch_diagnostics(const llb_ctx& c, const void* mom, void* scratch,
 }
 
 }  // namespace llb
+// ---------------------------------------------------------------------------
+// Diagnostics without allocation.
+//
+// Some callers cannot allocate device memory where they need the diagnostics:
+// code running while a stream is being captured into a CUDA graph (a
+// cudaMalloc there breaks the capture), allocator-owning frameworks and
+// real-time loops that forbid allocation on the hot path, and embedders whose
+// memory budget is fixed in advance.  For them the reduction below keeps its
+// scratch (one row of partial sums per block plus the result) in a
+// file-scope device array of fixed size, reserved when the library is loaded
+// on a device and held until the process exits.
+namespace llb {
+namespace {
+
+constexpr int kStaticRows = 4096;                       // partial-sum rows (one per block)
+constexpr size_t kStaticNodesPerRow = (size_t)kDiagThreads * 64;
+constexpr size_t kStaticMaxNodes = (size_t)kStaticRows * kStaticNodesPerRow;  // 67,108,864 nodes
+
+struct StaticScratch {
+    double rows[kStaticRows * kRow];
+    llb_diag out;
+};
+
+// 256 KB of scratch per device.  Every call on a device reuses it: calls that
+// overlap on the GPU (different streams, or different host threads without
+// ordering) race on it.  Each call writes every row it later reads and the
+// whole result, so no part of it has to be cleared between calls.
+static __device__ __align__(256) StaticScratch g_diag_scratch;
+
+// Partial sums of canonical one-component moments (rho, j, P), dense layout:
+// block b reduces nodes [b * kStaticNodesPerRow, (b + 1) * kStaticNodesPerRow).
+template <class T>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial_canonical(const T* __restrict__ m, size_t N,
+                                                                         double* __restrict__ rows) {
+    Part p;
+    part_init(p);
+    const size_t lo = (size_t)blockIdx.x * kStaticNodesPerRow;
+    const size_t hi = lo + kStaticNodesPerRow < N ? lo + kStaticNodesPerRow : N;
+    for (size_t i = lo + threadIdx.x; i < hi; i += kDiagThreads) {
+        const double rho = (double)m[i];
+        const double d = rho - 1.0;
+        const double jx = (double)m[N + i], jy = (double)m[2 * N + i], jz = (double)m[3 * N + i];
+        p.v[0] += d;
+        p.v[1] += jx;
+        p.v[2] += jy;
+        p.v[3] += jz;
+        if (rho > 0.5) {
+            p.v[4] += rho;
+            p.v[5] += 1.0;
+        }
+        p.v[6] = fmin(p.v[6], rho);
+        bool finite = isfinite(rho) && isfinite(jx) && isfinite(jy) && isfinite(jz);
+#pragma unroll
+        for (int f = 4; f < 10; ++f) finite = finite && isfinite((double)m[f * N + i]);
+        if (!finite) p.v[7] = 1.0;
+    }
+    p = block_reduce(p);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kRow; ++k) rows[(size_t)blockIdx.x * kRow + k] = p.v[k];
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+StaticScratch* g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace llb
+
+extern "C" int llb_diagnostics_noalloc(const void* dev_m, int dtype, int nx, int ny, int nz, void* stream,
+                                       llb_diag* host_out) {
+    using namespace llb;
+    if (!dev_m || !host_out || (dtype != LLB_F64 && dtype != LLB_F32) || nx < 1 || ny < 1 || nz < 1)
+        return LLB_EINVAL;
+    const size_t N = (size_t)nx * ny * nz;
+    if (N > kStaticMaxNodes) return LLB_EINVAL;  // more nodes than the fixed scratch can reduce
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return LLB_ECUDA;
+    }
+    StaticScratch* scratch = nullptr;
+    {
+        // once per device, with that device current: the device address of the
+        // array (its name in host code is only a host-side handle)
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_diag_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LLB_ECUDA;
+            }
+            g_static_ptr[dev] = static_cast<StaticScratch*>(p);
+        }
+        scratch = g_static_ptr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nb = (int)((N + kStaticNodesPerRow - 1) / kStaticNodesPerRow);
+    if (dtype == LLB_F64)
+        k_diag_partial_canonical<double><<<nb, kDiagThreads, 0, s>>>(static_cast<const double*>(dev_m), N,
+                                                                      scratch->rows);
+    else
+        k_diag_partial_canonical<float><<<nb, kDiagThreads, 0, s>>>(static_cast<const float*>(dev_m), N,
+                                                                     scratch->rows);
+    if (cudaGetLastError() != cudaSuccess) return LLB_ECUDA;
+    k_diag_final<<<1, kDiagThreads, 0, s>>>(scratch->rows, nb, N, &scratch->out);
+    if (cudaGetLastError() != cudaSuccess) return LLB_ECUDA;
+    if (cudaMemcpyAsync(host_out, &scratch->out, sizeof(llb_diag), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return LLB_ECUDA;
+    }
+    return LLB_OK;
+}

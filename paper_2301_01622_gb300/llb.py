@@ -73,6 +73,8 @@ _SIGS = {
     "llb_get_moments_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "llb_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(llb_diag)]),
     "llb_synchronize": (C.c_int, [C.c_void_p]),
+    "llb_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                          C.POINTER(llb_diag)]),
     "llb_steps_done": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "llb_state_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "llb_status_string": (C.c_char_p, [C.c_int]),
@@ -218,6 +220,15 @@ def llb_get_moments_device(ctx, dev_out):
 def llb_diagnostics(ctx) -> dict:
     d = llb_diag()
     _check(lib().llb_diagnostics(ctx, C.byref(d)), "llb_diagnostics", ctx)
+    return d.as_dict()
+
+
+def llb_diagnostics_noalloc(dev_m, nx, ny, nz, stream=None) -> dict:
+    """Diagnostics of canonical moments already on the device, without any
+    device allocation (fixed scratch inside the library; see include/llb.h)."""
+    d = llb_diag()
+    _check(lib().llb_diagnostics_noalloc(_ptr(dev_m), _dtype_code(dev_m), nx, ny, nz, stream, C.byref(d)),
+           "llb_diagnostics_noalloc")
     return d.as_dict()
 
 
