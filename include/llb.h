@@ -192,7 +192,7 @@ LLB_API int llb_diagnostics(llb_ctx* ctx, llb_diag* out);
  * the device allocator, real-time loops that forbid allocation on the hot
  * path, and embedders with a fixed memory budget.  This call allocates
  * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
- * scratch is a fixed 256 KB array in device memory that every GPU which
+ * scratch is a fixed 288 KB array in device memory that every GPU which
  * loads the library holds until the process exits.
  *
  * dev_m: nx*ny*nz*10 elements of type dtype (LLB_F32 or LLB_F64), caller-owned.

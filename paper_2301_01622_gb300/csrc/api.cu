@@ -72,8 +72,15 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     }
     if (p.variant < 0 || p.variant > 4) { *why = "variant must be in 0..4"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
-        *why = "two-component model not available in this build";
-        return LLB_EINVAL;
+        if (p.scheme != LLB_SCHEME_MOMENT) { *why = "two components run only the moment-only scheme"; return LLB_EINVAL; }
+        if (nx < 4 || ny < 4 || nz < 4) { *why = "two components need nx, ny, nz >= 4"; return LLB_EINVAL; }
+        if (p.kernel == LLB_KERNEL_DIRECT || p.kernel == LLB_KERNEL_TMA) {
+            *why = "two components run the tiled kernel"; return LLB_EINVAL;
+        }
+        if (!(p.beta >= 0.0) || !std::isfinite(p.A_s) || !std::isfinite(p.A_h) || !(p.g_min > 0.0) || p.h_c < 0 ||
+            p.h_c > 8) {
+            *why = "bad two-component parameters"; return LLB_EINVAL;
+        }
     }
     const double n = (double)nx * ny * nz;
     if (n > 4.0e9) { *why = "domain too large"; return LLB_EINVAL; }
@@ -92,7 +99,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     c->elem = elem_size(p.storage);
     // the moment-only state carries periodic ghosts (TMA tile boxes); the
     // population schemes keep dense populations and dense moment temporaries
-    c->lay = make_layout(nx, ny, nz, c->scheme == LLB_SCHEME_MOMENT);
+    c->lay = make_layout(nx, ny, nz, c->scheme == LLB_SCHEME_MOMENT, c->ncomp == 2 ? 2 : 1);
     c->state_bytes = c->scheme == LLB_SCHEME_MOMENT ? (size_t)c->nf * c->lay.fs * c->elem
                                                     : (size_t)c->nf * c->N * c->elem;
     return LLB_OK;
@@ -196,6 +203,7 @@ int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p
     if (ncomp != 1 && ncomp != 2) return LLB_EINVAL;
     c.ncomp = ncomp;
     c.nf = fields_of(c);
+    if (ncomp == 2 && c.scheme == LLB_SCHEME_MOMENT) c.lay = make_layout(nx, ny, nz, true, 2);
     out->fields = c.nf;
     out->arrays = 2 * c.nf;
     out->bytes_per_node = 2 * (size_t)c.nf * c.elem;
@@ -249,12 +257,17 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
         }
         if (cudaMemsetAsync(c->buf[b], 0, bytes, c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
     }
-    c->diag_scratch_bytes = (size_t)diag_blocks(*c) * 8 * sizeof(double) + 256;
+    c->diag_scratch_bytes = (size_t)diag_blocks(*c) * 16 * sizeof(double) + 256;
     if (cudaMalloc(&c->diag_scratch, c->diag_scratch_bytes + sizeof(llb_diag)) != cudaSuccess) { cudaGetLastError(); c->diag_scratch = nullptr; return bail(LLB_ENOMEM); }
     if (cudaMalloc(&c->flag_dev, 2 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); c->flag_dev = nullptr; return bail(LLB_ENOMEM); }
     c->err_dev = static_cast<int*>(c->flag_dev) + 1;
     if (cudaMemsetAsync(c->flag_dev, 0, 2 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
-    if (c->scheme == LLB_SCHEME_MOMENT) {
+    if (c->scheme == LLB_SCHEME_MOMENT && c->ncomp == 2) {
+        c->tile_ctas = cg_tiled_ctas(*c);
+        cudaGetLastError();
+        if (c->tile_ctas <= 0) return bail(LLB_EINVAL);
+        c->kernel = LLB_KERNEL_TILED;
+    } else if (c->scheme == LLB_SCHEME_MOMENT) {
         c->tile_ctas = moment_tiled_ctas(*c);
         cudaGetLastError();
         c->tmap_ok = moment_tma_encode(*c, c->buf[0], &c->tmap[0]) && moment_tma_encode(*c, c->buf[1], &c->tmap[1]);
@@ -333,7 +346,9 @@ int llb_step(llb_ctx* c, int nsteps) {
         const void* in = c->buf[c->cur];
         void* out = c->buf[1 - c->cur];
         cudaError_t e;
-        if (c->scheme == LLB_SCHEME_MOMENT)
+        if (c->ncomp == 2)
+            e = launch_cg_tiled(*c, in, out);
+        else if (c->scheme == LLB_SCHEME_MOMENT)
             e = c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, c->cur, out)
                 : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
                                                 : launch_moment_direct(*c, in, out);

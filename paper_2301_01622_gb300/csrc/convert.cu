@@ -5,6 +5,8 @@
 // shifted storage:           d = rho - 1, j, A = P - cs^2 rho I
 // Equilibrium (second moment of Eq. eq-part): P^eq = cs^2 rho I + rho u u, so
 // A^eq = rho u u.  All conversions compute in FP64 and round once.
+// Two components: canonical rho1, rho2, j, P; state rho1, d = rho1 + rho2 - 1,
+// j, A (rho1 needs no shift: it lies in [0, rho]).
 // Canonical buffers are dense; the shifted state follows the context's
 // Layout (padded with periodic ghosts for the moment scheme), and every
 // write to it also writes the node's ghost copies.
@@ -101,6 +103,73 @@ __global__ void k_equilibrium(const void* __restrict__ rho_p, const void* __rest
     }
 }
 
+// Two components.  canonical: rho1, rho2, j (3), P (6); state: rho1, d = rho1 + rho2 - 1,
+// j (3), A = P - cs^2 rho I (6).
+template <class T>
+__device__ __forceinline__ void put11(T* __restrict__ st, const Layout& L, int x, int y, int z, const double* v) {
+    for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
+        const size_t j = L.at(gx, gy, z);
+#pragma unroll
+        for (int f = 0; f < 11; ++f) st[f * L.fs + j] = (T)v[f];
+    });
+}
+
+template <class T>
+__global__ void k_canon_to_shifted2(const void* __restrict__ canon, int cdt, T* __restrict__ st, Layout L,
+                                    int* bad) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        double v[11];
+#pragma unroll
+        for (int f = 0; f < 11; ++f) v[f] = rdt(canon, f * N + i, cdt);
+        const double rho = v[0] + v[1];
+        bool b = bad_rho(rho) || !(v[0] >= 0.0) || !(v[1] >= 0.0);
+#pragma unroll
+        for (int f = 2; f < 11; ++f) b = b || !isfinite(v[f]);
+        if (b && bad) atomicOr(bad, 1);
+        const double o[11] = {v[0], rho - 1.0, v[2], v[3], v[4], v[5] - kCs2 * rho, v[6] - kCs2 * rho,
+                              v[7] - kCs2 * rho, v[8], v[9], v[10]};
+        int x, y, z;
+        decode(L, i, x, y, z);
+        put11(st, L, x, y, z, o);
+    }
+}
+
+template <class T>
+__global__ void k_shifted_to_canon2(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        decode(L, i, x, y, z);
+        const size_t j = L.at(x, y, z);
+        const double r1 = (double)st[j];
+        const double rho = 1.0 + (double)st[L.fs + j];
+        wrt(canon, i, cdt, r1);
+        wrt(canon, N + i, cdt, rho - r1);
+        for (int f = 2; f < 5; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
+        for (int f = 5; f < 8; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j] + kCs2 * rho);
+        for (int f = 8; f < 11; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
+    }
+}
+
+template <class T>
+__global__ void k_equilibrium2(const void* __restrict__ rho_p, const void* __restrict__ u_p, int dt,
+                               T* __restrict__ st, Layout L, int* bad) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const double r1 = rdt(rho_p, i, dt), r2 = rdt(rho_p, N + i, dt);
+        const double rho = r1 + r2;
+        const double ux = rdt(u_p, i, dt), uy = rdt(u_p, N + i, dt), uz = rdt(u_p, 2 * N + i, dt);
+        if ((bad_rho(rho) || !(r1 >= 0.0) || !(r2 >= 0.0) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) && bad)
+            atomicOr(bad, 1);
+        const double o[11] = {r1, rho - 1.0, rho * ux, rho * uy, rho * uz, rho * ux * ux, rho * uy * uy,
+                              rho * uz * uz, rho * ux * uy, rho * ux * uz, rho * uy * uz};
+        int x, y, z;
+        decode(L, i, x, y, z);
+        put11(st, L, x, y, z, o);
+    }
+}
+
 int grid_for(const llb_ctx& c) {
     const size_t want = (c.N + 255) / 256;
     const size_t cap = (size_t)(c.num_sms > 0 ? c.num_sms : 148) * 8;
@@ -110,6 +179,13 @@ int grid_for(const llb_ctx& c) {
 }  // namespace
 
 cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int cdt, void* st, int* bad) {
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_canon_to_shifted2<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
+        else
+            k_canon_to_shifted2<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad);
+        return cudaGetLastError();
+    }
     if (c.storage == LLB_F64)
         k_canon_to_shifted<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
     else
@@ -118,6 +194,13 @@ cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int
 }
 
 cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* canon, int cdt) {
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_shifted_to_canon2<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
+        else
+            k_shifted_to_canon2<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay);
+        return cudaGetLastError();
+    }
     if (c.storage == LLB_F64)
         k_shifted_to_canon<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
     else
@@ -126,6 +209,13 @@ cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* 
 }
 
 cudaError_t launch_equilibrium(const llb_ctx& c, const void* rho, const void* u, int dt, void* st, int* bad) {
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_equilibrium2<double><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<double*>(st), c.lay, bad);
+        else
+            k_equilibrium2<float><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<float*>(st), c.lay, bad);
+        return cudaGetLastError();
+    }
     if (c.storage == LLB_F64)
         k_equilibrium<double><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<double*>(st), c.lay, bad);
     else

@@ -20,7 +20,7 @@ namespace llb {
 namespace {
 
 constexpr int kDiagThreads = 256;
-constexpr int kRow = 8;  // sum d, sum jx, sum jy, sum jz, sum rho_in, n_in, min rho, nonfinite
+constexpr int kRow = 9;  // sum d, sum jx, sum jy, sum jz, sum rho_in, n_in, min rho, nonfinite, sum rho1
 
 struct Part {
     double v[kRow];
@@ -37,6 +37,7 @@ __device__ __forceinline__ void part_merge(Part& a, const Part& b) {
     for (int k = 0; k < 6; ++k) a.v[k] += b.v[k];
     a.v[6] = fmin(a.v[6], b.v[6]);
     a.v[7] = fmax(a.v[7], b.v[7]);
+    a.v[8] += b.v[8];
 }
 
 __device__ __forceinline__ Part warp_reduce(Part p) {
@@ -68,31 +69,38 @@ __device__ Part block_reduce(Part p) {
     return p;
 }
 
-template <class T>
+// Row of partial sums: (sum d, sum j, sum of the droplet density over nodes
+// where it exceeds 0.5, their count, min rho, non-finite flag, sum rho1).
+// The droplet density is rho for one component and rho1 for two (state
+// rho1, d, j, A; rho2 = 1 + d - rho1 is recovered from the sums).
+template <class T, int NC>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restrict__ m, Layout L,
                                                                double* __restrict__ rows) {
     Part p;
     part_init(p);
     const size_t N = (size_t)L.nx * L.ny * L.nz, F = L.fs;
+    constexpr int o = NC == 2 ? 1 : 0;  // field offset of d
     for (size_t n = blockIdx.x * (size_t)kDiagThreads + threadIdx.x; n < N; n += (size_t)gridDim.x * kDiagThreads) {
         const int x = (int)(n % L.nx);
         const size_t r = n / L.nx;
         const size_t i = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
-        const double d = (double)m[i];
-        const double jx = (double)m[F + i], jy = (double)m[2 * F + i], jz = (double)m[3 * F + i];
+        const double d = (double)m[o * F + i];
+        const double jx = (double)m[(o + 1) * F + i], jy = (double)m[(o + 2) * F + i], jz = (double)m[(o + 3) * F + i];
         const double rho = 1.0 + d;
+        const double drop = NC == 2 ? (double)m[i] : rho;
         p.v[0] += d;
         p.v[1] += jx;
         p.v[2] += jy;
         p.v[3] += jz;
-        if (rho > 0.5) {
-            p.v[4] += rho;
+        if (drop > 0.5) {
+            p.v[4] += drop;
             p.v[5] += 1.0;
         }
         p.v[6] = fmin(p.v[6], rho);
-        bool finite = isfinite(d) && isfinite(jx) && isfinite(jy) && isfinite(jz);
+        if (NC == 2) p.v[8] += drop;
+        bool finite = isfinite(d) && isfinite(jx) && isfinite(jy) && isfinite(jz) && isfinite(drop);
 #pragma unroll
-        for (int f = 4; f < 10; ++f) finite = finite && isfinite((double)m[f * F + i]);
+        for (int f = o + 4; f < o + 10; ++f) finite = finite && isfinite((double)m[f * F + i]);
         if (!finite) p.v[7] = 1.0;
     }
     p = block_reduce(p);
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
 }
 
 __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* __restrict__ rows, int nrows, size_t N,
-                                                             llb_diag* __restrict__ out) {
+                                                             int ncomp, llb_diag* __restrict__ out) {
     Part p;
     part_init(p);
     for (int r = threadIdx.x; r < nrows; r += kDiagThreads) {
@@ -111,8 +119,13 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* __res
     }
     p = block_reduce(p);
     if (threadIdx.x == 0) {
-        out->mass[0] = (double)N + p.v[0];
-        out->mass[1] = 0.0;
+        if (ncomp == 2) {
+            out->mass[0] = p.v[8];
+            out->mass[1] = (double)N + p.v[0] - p.v[8];
+        } else {
+            out->mass[0] = (double)N + p.v[0];
+            out->mass[1] = 0.0;
+        }
         out->momentum[0] = p.v[1];
         out->momentum[1] = p.v[2];
         out->momentum[2] = p.v[3];
@@ -137,17 +150,25 @@ int diag_blocks(const llb_ctx& c) {
 cudaError_t launch_diagnostics(const llb_ctx& c, const void* mom, void* scratch, llb_diag* dev_out) {
     const int nb = diag_blocks(c);
     double* rows = static_cast<double*>(scratch);
-    if (c.storage == LLB_F64)
-        k_diag_partial<double><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.lay, rows);
-    else
-        k_diag_partial<float><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const float*>(mom), c.lay, rows);
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_diag_partial<double, 2><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.lay, rows);
+        else
+            k_diag_partial<float, 2><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const float*>(mom), c.lay, rows);
+    } else {
+        if (c.storage == LLB_F64)
+            k_diag_partial<double, 1><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.lay, rows);
+        else
+            k_diag_partial<float, 1><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const float*>(mom), c.lay, rows);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_diag_final<<<1, kDiagThreads, 0, c.stream>>>(rows, nb, c.N, dev_out);
+    k_diag_final<<<1, kDiagThreads, 0, c.stream>>>(rows, nb, c.N, c.ncomp, dev_out);
     return cudaGetLastError();
 }
 
 }  // namespace llb
+
 // ---------------------------------------------------------------------------
 // Diagnostics without allocation.
 //
@@ -171,7 +192,7 @@ struct StaticScratch {
     llb_diag out;
 };
 
-// 256 KB of scratch per device.  Every call on a device reuses it: calls that
+// 288 KB of scratch per device.  Every call on a device reuses it: calls that
 // overlap on the GPU (different streams, or different host threads without
 // ordering) race on it.  Each call writes every row it later reads and the
 // whole result, so no part of it has to be cleared between calls.
@@ -252,7 +273,7 @@ extern "C" int llb_diagnostics_noalloc(const void* dev_m, int dtype, int nx, int
         k_diag_partial_canonical<float><<<nb, kDiagThreads, 0, s>>>(static_cast<const float*>(dev_m), N,
                                                                      scratch->rows);
     if (cudaGetLastError() != cudaSuccess) return LLB_ECUDA;
-    k_diag_final<<<1, kDiagThreads, 0, s>>>(scratch->rows, nb, N, &scratch->out);
+    k_diag_final<<<1, kDiagThreads, 0, s>>>(scratch->rows, nb, N, 1, &scratch->out);
     if (cudaGetLastError() != cudaSuccess) return LLB_ECUDA;
     if (cudaMemcpyAsync(host_out, &scratch->out, sizeof(llb_diag), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -65,6 +65,10 @@ int moment_tma_ctas(const llb_ctx& c);
 // Encode the TMA descriptor of a moment buffer; false if TMA cannot serve this shape.
 bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out);
 
+// Two-component colour-gradient moment-only step (cg_step.cu)
+int cg_tiled_ctas(const llb_ctx& c);
+cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out);
+
 // Population-storing baselines (population_step.cu)
 cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);
 // state <- populations reconstructed from shifted moments (un-streamed so a pull reads them)

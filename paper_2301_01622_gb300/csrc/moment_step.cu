@@ -304,23 +304,26 @@ __device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T
     add_plane<L, T, 1>(g, g_p, Z);
 }
 
-// Halo node handled by thread t < NH and its role.  Warp-uniform where the
-// tile width allows: threads [0, BX) take the row above the tile, [BX, 2 BX)
-// the row below, then the left and right columns and the four corners.
-enum HaloRole { kNone, kTop, kBottom, kLeft, kRight, kTL, kTR, kBL, kBR };
+// Halo node handled by thread t < NH and its role.  Threads [0, BX) take the
+// row above the tile and publish only c_y = +1, threads [BX, 2 BX) the row
+// below (c_y = -1); both roles are warp-uniform when BX is a multiple of 32.
+// The remaining threads take the left and right columns and the corners
+// and publish every crossing direction: one code path for the whole warp
+// (the directions nobody pulls are simply never read).
+enum HaloRole { kNone, kTop, kBottom, kSide };
 
 template <int BX, int BY>
 __device__ __forceinline__ int halo_node(int t, int& hx, int& hy) {
     if (t < BX) { hx = t + 1; hy = 0; return kTop; }
     if (t < 2 * BX) { hx = t - BX + 1; hy = BY + 1; return kBottom; }
     const int s = t - 2 * BX;
-    if (s < BY) { hx = 0; hy = s + 1; return kLeft; }
-    if (s < 2 * BY) { hx = BX + 1; hy = s - BY + 1; return kRight; }
+    if (s < BY) { hx = 0; hy = s + 1; return kSide; }
+    if (s < 2 * BY) { hx = BX + 1; hy = s - BY + 1; return kSide; }
     switch (s - 2 * BY) {
-        case 0: hx = 0; hy = 0; return kTL;
-        case 1: hx = BX + 1; hy = 0; return kTR;
-        case 2: hx = 0; hy = BY + 1; return kBL;
-        case 3: hx = BX + 1; hy = BY + 1; return kBR;
+        case 0: hx = 0; hy = 0; return kSide;
+        case 1: hx = BX + 1; hy = 0; return kSide;
+        case 2: hx = 0; hy = BY + 1; return kSide;
+        case 3: hx = BX + 1; hy = BY + 1; return kSide;
         default: hx = 0; hy = 0; return kNone;
     }
 }
@@ -328,17 +331,9 @@ __device__ __forceinline__ int halo_node(int t, int& hx, int& hy) {
 // Publish a collided halo node: only the directions its role feeds.
 template <class L, class T, int HN>
 __device__ __forceinline__ void publish_halo(T* __restrict__ G, int n, int role, const Mom<T>& c) {
-    switch (role) {
-        case kTop: publish<L, T, HN, kAny, 1>(G, n, c); break;
-        case kBottom: publish<L, T, HN, kAny, -1>(G, n, c); break;
-        case kLeft: publish<L, T, HN, 1, kAny>(G, n, c); break;
-        case kRight: publish<L, T, HN, -1, kAny>(G, n, c); break;
-        case kTL: publish<L, T, HN, 1, 1>(G, n, c); break;
-        case kTR: publish<L, T, HN, -1, 1>(G, n, c); break;
-        case kBL: publish<L, T, HN, 1, -1>(G, n, c); break;
-        case kBR: publish<L, T, HN, -1, -1>(G, n, c); break;
-        default: break;
-    }
+    if (role == kTop) publish<L, T, HN, kAny, 1>(G, n, c);
+    else if (role == kBottom) publish<L, T, HN, kAny, -1>(G, n, c);
+    else if (role == kSide) publish<L, T, HN>(G, n, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,123 @@
+"""GPU parity of the two-component moment-only step (colour gradient,
+recolouring, near-contact force) against the FP64 oracle."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import D3Q19, D3Q27, lb
+from oracle import two_component as tc
+from paper_2301_01622_gb300 import inputs, llb
+
+from gpu_helpers import assert_groups, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+LAT = {19: D3Q19, 27: D3Q27}
+GROUPS_2 = {"rho": slice(0, 2), "j": slice(2, 5), "P": slice(5, 11)}
+
+
+def _moments(r1, r2, u):
+    tot = lb.equilibrium_moments(r1 + r2, u)
+    return np.concatenate([r1[None], r2[None], tot[1:]])
+
+
+def _pair(shape, radius, gap, speed, impact):
+    nx, ny, nz = shape
+    c1 = (nx / 2 - radius - gap / 2, ny / 2 - impact / 2, nz / 2)
+    c2 = (nx / 2 + radius + gap / 2, ny / 2 + impact / 2, nz / 2)
+    return inputs.droplets(nx, ny, nz, [c1, c2], [radius, radius], [(speed, 0, 0), (-speed, 0, 0)])
+
+
+def _params(prm, storage):
+    return dict(ncomp=2, storage=storage, beta=prm.beta, A_s=prm.A_s, A_h=prm.A_h,
+                g_min=prm.g_min if storage == llb.LLB_F64 else 1e-6, h_c=prm.h_c)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_pair(q, shape, radius, gap, speed, impact, tau, steps, A_h, g_min):
+    r1, r2, u = _pair(shape, radius, gap, speed, impact)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=A_h, h_c=3, g_min=g_min)
+    return tc.run_moment_only(_moments(r1, r2, u), LAT[q], tau, prm, steps)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("A_h", [0.01, 0.0], ids=["nci", "no-nci"])
+def test_droplet_pair_fp64(q, A_h):
+    """Nearly touching off-axis pair, 40 x 24 x 20, 20 steps, FP64: 1e-12."""
+    shape, steps, tau = (40, 24, 20), 20, 0.9
+    args = (q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, A_h, 1e-8)
+    ref = _oracle_pair(*args)
+    if A_h:
+        cf = tc.CollisionFields(_moments(*_pair(shape, 5.0, 2.5, 0.03, 2.0)), LAT[q], tau,
+                                tc.CGParams(A_h=A_h))
+        assert cf.near.any()
+    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=A_h, h_c=3, g_min=1e-8)
+    got, used = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, **_params(prm, llb.LLB_F64))
+    assert used == llb.LLB_KERNEL_TILED
+    assert_groups(got, ref, 1e-12, GROUPS_2, what=f"D3Q{q} A_h={A_h}")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_droplet_pair_fp32(q):
+    """Same pair without the near-contact decision, FP32 storage, 100 steps: 1e-5."""
+    shape, steps, tau = (40, 24, 20), 100, 0.9
+    ref = _oracle_pair(q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, 0.0, 1e-8)
+    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.0, h_c=3)
+    got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, **_params(prm, llb.LLB_F32))
+    assert_groups(got, ref, 1e-5, GROUPS_2, what=f"D3Q{q} fp32")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_droplet_pair_fp32_nci_short(q):
+    """With the near-contact force on, FP32, 5 steps: 1e-5 (a decision that FP32
+    rounding flips would show as an O(A_h |G|) jump, far above the tolerance)."""
+    shape, steps, tau = (40, 24, 20), 5, 0.9
+    ref = _oracle_pair(q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, 0.01, 1e-8)
+    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.01, h_c=3)
+    got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, **_params(prm, llb.LLB_F32))
+    assert_groups(got, ref, 1e-5, GROUPS_2, what=f"D3Q{q} fp32 nci")
+
+
+@pytest.mark.parametrize("shape", [(37, 19, 11), (64, 9, 6), (4, 4, 4), (33, 17, 5)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("q", [19, 27])
+def test_random_fields_ragged_fp64(shape, q):
+    """Random 11-field moments (gradients everywhere, detector active), ragged
+    multi-tile boxes and the 4-node minimum: 1e-12 after 3 steps."""
+    nx, ny, nz = shape
+    m0 = inputs.random_moments(nx, ny, nz, seed=nx + 7 * ny + 31 * nz, nfields=11)
+    prm = tc.CGParams(beta=0.6, A_s=0.03, A_h=0.02, h_c=2, g_min=1e-8)
+    ref = tc.run_moment_only(m0, LAT[q], 0.8, prm, 3)
+    got, _ = run_gpu(shape, q, 0.8, 3, m0=m0, **_params(prm, llb.LLB_F64))
+    assert_groups(got, ref, 1e-12, GROUPS_2, what=f"{shape} D3Q{q}")
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_colour_conservation_and_diagnostics(q):
+    """Each colour's mass is conserved; llb_diagnostics reports rho1 and rho2
+    masses and <rho1>_{rho1 > 0.5} like the oracle."""
+    shape = (48, 32, 32)
+    r1, r2, u = _pair(shape, 7.0, 3.0, 0.04, 3.0)
+    p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F64, A_h=0.01, A_s=0.02)
+    ctx = llb.llb_create(*shape, q, 1.0, p)
+    try:
+        llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
+        d0 = llb.llb_diagnostics(ctx)
+        llb.llb_step(ctx, 60)
+        d1 = llb.llb_diagnostics(ctx)
+        m = llb.llb_get_moments(ctx, np.empty((11,) + shape[::-1]))
+    finally:
+        llb.llb_destroy(ctx)
+    from oracle import diagnostics as odg
+    ref = odg.diagnostics(m, ncomp=2)
+    n = np.prod(shape)
+    assert abs(d0["mass"][0] - r1.sum()) < 1e-9 and abs(d0["mass"][1] - r2.sum()) < 1e-9
+    assert abs(d1["mass"][0] - d0["mass"][0]) < 1e-10 * n
+    assert abs(d1["mass"][1] - d0["mass"][1]) < 1e-10 * n
+    assert d1["n_in"] == ref["n_in"]
+    assert abs(d1["rho1_avg"] - ref["rho1_avg"]) < 1e-12
+    assert abs(d1["mass"][0] - ref["mass"][0]) < 1e-10 * n
