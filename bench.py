@@ -52,6 +52,8 @@ def parse():
                     help="moment-only kernel (auto = the library's choice)")
     ap.add_argument("--variant", type=int, default=0, help="TMA kernel variant (tuning)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="lattice of the main line")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds the reference arm (host oracle) may spend on its timed steps")
     return ap.parse_args()
 
 
@@ -361,7 +363,7 @@ def reference_arm(args, rank):
 
     if rank != 0:
         return None
-    budget_s = 150.0
+    budget_s = getattr(args, "ref_budget", 150.0)
     per_plane = 0.03
     nzs = int(max(1, min(NZ, budget_s / max(1, args.steps + args.warmup) / per_plane)))
     rho, u = oracle_sample(nzs)
