@@ -30,7 +30,9 @@ repository's design notes, one per step:
        S_i = w_i [(c_i - u_F)/cs^2 + (c_i.u_F) c_i / cs^4] . F
    (for F = 0 this is Eq. coll2), plus the colour-gradient perturbation
        Delta_i = (A_s / 2) |G| [w_i (c_i.n)^2 - w_i cs^2]
-   applied to these populations (Sec. III A, last sentence).
+   applied to these populations (Sec. III A, last sentence) where the normal
+   is defined (|G| >= g_min); elsewhere Delta_i = 0 (with n = 0 the bracket
+   would not sum to zero and would create mass).
 4. recolouring of the collided populations (Sec. III A):
        h1'_i = (rho1/rho) h'_i + beta (rho1 rho2 / rho) w_i (c_i.n) / |c_i|   (0 for c_i = 0),
        h2'_i = h'_i - h1'_i.
@@ -168,7 +170,8 @@ def collided_direction(cf: CollisionFields, lat: Lattice, i: int):
     uFdot = u[0] * F[0] + u[1] * F[1] + u[2] * F[2]
     S = w * ((cF - uFdot) / CS2 + (c[0] * u[0] + c[1] * u[1] + c[2] * u[2]) * cF / (CS2 * CS2))
     cn = c[0] * cf.n[0] + c[1] * cf.n[1] + c[2] * cf.n[2]
-    pert = 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2)
+    # the perturbation acts only where the interface normal is defined
+    pert = np.where(cf.iface, 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2), 0.0)
     hp = (1.0 - om) * h + om * heq + (1.0 - 0.5 * om) * S + pert          # Eq. (coll) + forcing + perturbation
     cnorm = np.sqrt((c * c).sum())
     recol = 0.0 if cnorm == 0 else cf.prm.beta * (cf.rho1 * cf.rho2 / rho) * w * cn / cnorm

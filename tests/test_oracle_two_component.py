@@ -185,6 +185,20 @@ def test_recolouring_keeps_interface_sharp():
     assert np.abs(p7 - profiles[0]).max() < 1e-3      # stationary
 
 
+def test_perturbation_vanishes_off_the_interface():
+    """Below g_min the normal is undefined and the perturbation must not act:
+    a uniform mixture (G = 0) with A_s != 0 keeps its mass and evolves exactly
+    like the one-component scheme."""
+    m = inputs.random_moments(5, 4, 3, seed=2, nfields=11)
+    frac = 0.3
+    rho = m[0] + m[1]
+    m[0], m[1] = frac * rho, (1 - frac) * rho
+    m[:, :, :, :] = m[:, :1, :1, :1]          # uniform field: G = 0 everywhere
+    out = tc.step_moment_only(m, D3Q19, 0.8, tc.CGParams(A_s=0.5, beta=0.7, A_h=0.0))
+    np.testing.assert_allclose(tc.total_moments(out), lb.step_moment_only(tc.total_moments(m), D3Q19, 0.8),
+                               rtol=0, atol=1e-15)
+
+
 def test_count_droplets():
     a = np.zeros((10, 10, 20))
     a[3:6, 3:6, 2:5] = 1
