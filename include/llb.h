@@ -89,8 +89,9 @@ typedef struct llb_params {
     int storage;      /* LLB_F32 (default) or LLB_F64                        */
     int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
     int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
-    int variant;      /* tile/pipeline variant of LLB_KERNEL_TMA, 0..4 (0 = default);
-                         tuning only, every variant computes the same result  */
+    int variant;      /* tile/pipeline variant of the TMA and tiled kernels,
+                         0..4 (0 = default); tuning only, every variant
+                         computes the same result                            */
     /* two-component colour-gradient / near-contact parameters (Sec. III A-B) */
     double beta;      /* recolouring strength, default 0.7                   */
     double A_s;       /* surface-tension (perturbation) strength, default 0.01 */

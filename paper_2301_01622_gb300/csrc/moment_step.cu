@@ -349,8 +349,8 @@ struct Tiled {
     static_assert(NH <= NT, "halo must fit one node per thread");
 };
 
-template <class L, class T, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, 2)
+template <class L, class T, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
     k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, T omega, Sched sc) {
     using K = Tiled<L, T, BX, BY>;
     constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
@@ -574,7 +574,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // ---------------------------------------------------------------------------
 // Host side.
 
-constexpr int kBX = 32, kBY = 8;
 
 // TMA kernel variants (tile BX x BY, ring depth, CTAs per SM).  Variant 0 is
 // the default; the others exist for tuning sweeps (llb_params.variant).
@@ -596,29 +595,56 @@ cudaError_t run_direct(const llb_ctx& c, const void* in, void* out) {
     return cudaGetLastError();
 }
 
-template <class L, class T>
-int tiled_ctas(const llb_ctx& c) {
-    using K = Tiled<L, T, kBX, kBY>;
-    auto kern = k_moment_tiled<L, T, kBX, kBY>;
+// Plain-load tiled kernel variants (tile BX x BY, CTAs per SM the register
+// budget targets); variant 0 is the default.
+template <int BX_, int BY_, int MINB_>
+struct TiledShape {
+    static constexpr int BX = BX_, BY = BY_, MINB = MINB_;
+};
+template <class T, int V> struct TiledVariant { using type = TiledShape<32, 8, 2>; };
+template <> struct TiledVariant<float, 1> { using type = TiledShape<32, 8, 3>; };
+template <> struct TiledVariant<float, 2> { using type = TiledShape<32, 16, 1>; };
+template <> struct TiledVariant<float, 3> { using type = TiledShape<64, 4, 2>; };
+template <> struct TiledVariant<float, 4> { using type = TiledShape<32, 4, 4>; };
+template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
+
+template <class L, class T, class S>
+int tiled_ctas_c(const llb_ctx& c) {
+    using K = Tiled<L, T, S::BX, S::BY>;
+    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::NT, K::smem_bytes) != cudaSuccess ||
         per_sm < 1)
         return 0;
-    const Sched sc = plan(c.nx, c.ny, c.nz, kBX, kBY, per_sm * c.num_sms);
+    const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, per_sm * c.num_sms);
     return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
-template <class L, class T>
-cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) {
-    using K = Tiled<L, T, kBX, kBY>;
+template <class L, class T, class S>
+cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
+    using K = Tiled<L, T, S::BX, S::BY>;
     const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
-    const Sched sc = plan(c.nx, c.ny, c.nz, kBX, kBY, grid);
-    k_moment_tiled<L, T, kBX, kBY><<<grid, K::NT, K::smem_bytes, c.stream>>>(
+    const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, grid);
+    k_moment_tiled<L, T, S::BX, S::BY, S::MINB><<<grid, K::NT, K::smem_bytes, c.stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), c.lay, (T)c.omega, sc);
     return cudaGetLastError();
 }
+
+#define LLB_TILED_VARIANT(fn, ...)                                                           \
+    switch (c.variant) {                                                                     \
+        case 1: return fn<L, T, typename TiledVariant<T, 1>::type>(__VA_ARGS__);             \
+        case 2: return fn<L, T, typename TiledVariant<T, 2>::type>(__VA_ARGS__);             \
+        case 3: return fn<L, T, typename TiledVariant<T, 3>::type>(__VA_ARGS__);             \
+        case 4: return fn<L, T, typename TiledVariant<T, 4>::type>(__VA_ARGS__);             \
+        default: return fn<L, T, typename TiledVariant<T, 0>::type>(__VA_ARGS__);            \
+    }
+
+template <class L, class T>
+int tiled_ctas(const llb_ctx& c) { LLB_TILED_VARIANT(tiled_ctas_c, c) }
+template <class L, class T>
+cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) { LLB_TILED_VARIANT(run_tiled_c, c, in, out) }
 
 template <class L, class T, class C>
 int tma_ctas_c(const llb_ctx& c) {
