@@ -52,6 +52,7 @@ def parse():
                     help="moment-only kernel (auto = the library's choice)")
     ap.add_argument("--variant", type=int, default=0, help="TMA kernel variant (tuning)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="lattice of the main line")
+    ap.add_argument("--cg-variant", type=int, default=0, help="two-component kernel variant (tuning)")
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="seconds the reference arm (host oracle) may spend on its timed steps")
     return ap.parse_args()
@@ -260,6 +261,9 @@ def gpu_arm(args, rank, world, local):
         extra["moment_d3q27"] = run(27, llb.LLB_SCHEME_MOMENT)
         extra["population_d3q27"] = run(27, llb.LLB_SCHEME_POPULATION)
 
+    if not args.no_extra:
+        extra["two_component_d3q27"] = droplet_arm(args, llb, inputs, stream, world, peak)
+
     # end to end through the C ABI with pinned host buffers
     e2e = e2e_arm(args, llb, rho, u, stream, world)
 
@@ -276,6 +280,31 @@ def gpu_arm(args, rank, world, local):
     finally:
         llb.llb_destroy(ctx)
     return main, extra, e2e, {"ms": diag_ms, "mass": diag["mass"][0], "flags": diag["flags"]}, peak, peak_src
+
+
+def droplet_arm(args, llb, inputs, stream, world, peak):
+    """Two-component D3Q27 droplet collision, 384 x 192 x 192, FP32, tau = 1,
+    R = 30, +-0.05 along x, impact parameter 0.5 R, near-contact force on
+    (A_h = 0.01): MLUPS of the fused colour-gradient step (88 B/node)."""
+    import torch
+    nx, ny, nz = 384, 192, 192
+    r1, r2, u = inputs.droplet_pair(nx, ny, nz, 30.0, 0.05, 15.0)
+    p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F32, A_h=0.01, A_s=0.01, beta=0.7, stream=stream,
+                               variant=getattr(args, "cg_variant", 0))
+    ctx = llb.llb_create(nx, ny, nz, 27, 1.0, p)
+    try:
+        llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
+        steps = max(10, args.steps // 4)
+        ms, _ = time_steps(llb, ctx, steps, max(3, args.warmup), world)
+    finally:
+        llb.llb_destroy(ctx)
+    ms = reduce_max(ms, world)
+    nodes = nx * ny * nz
+    t = ms / 1e3 / steps
+    gbs = 88 * nodes / t / 1e9
+    return {"mlups": world * nodes / t / 1e6, "frac": gbs / peak, "achieved_gbs": gbs, "bytes_per_node": 88,
+            "ms_per_step": ms / steps, "steps": steps,
+            "workload": "384x192x192 D3Q27 two-component CG + near-contact, FP32, tau=1, R=30, U=+-0.05, b=0.5R"}
 
 
 def e2e_arm(args, llb, rho, u, stream, world):
@@ -430,6 +459,7 @@ def main():
         "population_d3q19": _short(extra.get("population_d3q19")),
         "moment_d3q27": _short(extra.get("moment_d3q27")),
         "population_d3q27": _short(extra.get("population_d3q27")),
+        "two_component_d3q27": extra.get("two_component_d3q27"),
         "speedup_vs_population_d3q19": (main_r["mlups"] / extra["population_d3q19"]["mlups"])
         if "population_d3q19" in extra else None,
         "diagnostics": diag,

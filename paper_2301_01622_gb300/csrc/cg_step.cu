@@ -344,7 +344,8 @@ struct CGCfg {
     static constexpr int NS = n_xy_shifted<L>();
     static constexpr size_t smem_bytes = sizeof(T) * (2 * (size_t)NS * HN1 + 3 * (size_t)HN2);
     static_assert(2 * BX + 2 * BY + 4 <= NT, "halo must fit one node per thread");
-    static_assert(HN2 <= 2 * NT, "phi region must fit two nodes per thread");
+    static constexpr int NJ = (HN2 + NT - 1) / NT;  // phi nodes per thread
+    static_assert(NJ <= 3, "phi region must fit three nodes per thread");
 };
 
 template <class L, class T, int BX, int BY>
@@ -367,9 +368,8 @@ __global__ void __launch_bounds__(BX * BY, 2)
     const int role2 = halo_role2<BX, BY>(t, hx2, hy2);
     const int n2 = hy2 * HX1 + hx2;
     const int b2 = (hy2 + 1) * HX2 + (hx2 + 1);
-    // phi nodes of this thread: j = t and j = t + NT inside the tile + 2 halo
-    const int j1 = t, j2 = t + NT;
-    const bool has_j2 = j2 < HN2;
+    // phi nodes of this thread: j = t + q NT (q < NJ) inside the tile + 2 halo
+    constexpr int NJ = C::NJ;
 
     for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
         const int chunk = it / sc.ntiles, tile = it - chunk * sc.ntiles;
@@ -379,20 +379,33 @@ __global__ void __launch_bounds__(BX * BY, 2)
         const int gx1 = pmod2(x0 + tx, nx), gy1 = pmod2(y0 + ty, ny);
         const int gx2 = pmod2(x0 - 1 + hx2, nx), gy2 = pmod2(y0 - 1 + hy2, ny);
         const size_t off1 = lay.at(gx1, gy1, 0), off2 = lay.at(gx2, gy2, 0);
-        const size_t offj1 = lay.at(pmod2(x0 - 2 + j1 % HX2, nx), pmod2(y0 - 2 + j1 / HX2, ny), 0);
-        const size_t offj2 = has_j2 ? lay.at(pmod2(x0 - 2 + j2 % HX2, nx), pmod2(y0 - 2 + j2 / HX2, ny), 0) : 0;
+        size_t offj[NJ];
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            const int j = t + q * NT;
+            offj[q] = j < HN2 ? lay.at(pmod2(x0 - 2 + j % HX2, nx), pmod2(y0 - 2 + j / HX2, ny), 0) : 0;
+        }
 
         // phi of planes za-2 and za-1 into ring slots 0 and 1 (slot of plane p: (p - za + 2) % 3)
         for (int pz = 0; pz < 2; ++pz) {
             const size_t zo = (size_t)pmod2(za - 2 + pz, nz) * plane;
-            PH[pz * HN2 + j1] = phi_of(__ldg(in + zo + offj1), __ldg(in + fs + zo + offj1));
-            if (has_j2) PH[pz * HN2 + j2] = phi_of(__ldg(in + zo + offj2), __ldg(in + fs + zo + offj2));
+#pragma unroll
+            for (int q = 0; q < NJ; ++q)
+                if (t + q * NT < HN2)
+                    PH[pz * HN2 + t + q * NT] = phi_of(__ldg(in + zo + offj[q]), __ldg(in + fs + zo + offj[q]));
         }
         // registers: phi inputs of plane za, moments of source plane za-1
         size_t zo = (size_t)pmod2(za, nz) * plane;
-        T pr1a = __ldg(in + zo + offj1), pda = __ldg(in + fs + zo + offj1);
-        T pr1b = T(0), pdb = T(0);
-        if (has_j2) { pr1b = __ldg(in + zo + offj2); pdb = __ldg(in + fs + zo + offj2); }
+        T pr1[NJ], pd[NJ];
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            pr1[q] = T(0);
+            pd[q] = T(0);
+            if (t + q * NT < HN2) {
+                pr1[q] = __ldg(in + zo + offj[q]);
+                pd[q] = __ldg(in + fs + zo + offj[q]);
+            }
+        }
         zo = (size_t)pmod2(za - 1, nz) * plane;
         Node2<T> m1 = load_node2(in, zo + off1, fs);
         Node2<T> m2 = m1;
@@ -403,14 +416,18 @@ __global__ void __launch_bounds__(BX * BY, 2)
         for (int s = za - 1; s <= zb; ++s) {
             // (a) phi of plane s+1 from registers; prefetch for the next plane
             const int slot_p = (s + 1 - za + 2) % 3;
-            PH[slot_p * HN2 + j1] = phi_of(pr1a, pda);
-            if (has_j2) PH[slot_p * HN2 + j2] = phi_of(pr1b, pdb);
+#pragma unroll
+            for (int q = 0; q < NJ; ++q)
+                if (t + q * NT < HN2) PH[slot_p * HN2 + t + q * NT] = phi_of(pr1[q], pd[q]);
             Node2<T> n1next = m1, n2next = m2;
             if (s + 1 <= zb) {
                 const size_t zq = (size_t)pmod2(s + 2, nz) * plane;
-                pr1a = __ldg(in + zq + offj1);
-                pda = __ldg(in + fs + zq + offj1);
-                if (has_j2) { pr1b = __ldg(in + zq + offj2); pdb = __ldg(in + fs + zq + offj2); }
+#pragma unroll
+                for (int q = 0; q < NJ; ++q)
+                    if (t + q * NT < HN2) {
+                        pr1[q] = __ldg(in + zq + offj[q]);
+                        pd[q] = __ldg(in + fs + zq + offj[q]);
+                    }
                 const size_t zn = (size_t)pmod2(s + 1, nz) * plane;
                 n1next = load_node2(in, zn + off1, fs);
                 if (role2) n2next = load_node2(in, zn + off2, fs);
@@ -473,10 +490,8 @@ Sched2 plan2(int nx, int ny, int nz, int BX, int BY, int grid) {
     return s;
 }
 
-constexpr int kBX2 = 32, kBY2 = 8;
-
-template <class L, class T>
-int cg_ctas_t(const llb_ctx& c) {
+template <class L, class T, int kBX2, int kBY2>
+int cg_ctas_v(const llb_ctx& c) {
     using C = CGCfg<L, T, kBX2, kBY2>;
     auto kern = k_cg_tiled<L, T, kBX2, kBY2>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) != cudaSuccess)
@@ -489,8 +504,8 @@ int cg_ctas_t(const llb_ctx& c) {
     return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
-template <class L, class T>
-cudaError_t cg_run_t(const llb_ctx& c, const void* in, void* out) {
+template <class L, class T, int kBX2, int kBY2>
+cudaError_t cg_run_v(const llb_ctx& c, const void* in, void* out) {
     using C = CGCfg<L, T, kBX2, kBY2>;
     const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
     const Sched2 sc = plan2(c.nx, c.ny, c.nz, kBX2, kBY2, grid);
@@ -505,6 +520,16 @@ cudaError_t cg_run_t(const llb_ctx& c, const void* in, void* out) {
     k_cg_tiled<L, T, kBX2, kBY2><<<grid, C::NT, C::smem_bytes, c.stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), c.lay, p, sc);
     return cudaGetLastError();
+}
+
+// Tile shapes: variant 0 = 64 x 4 (default), 1 = 32 x 8.
+template <class L, class T>
+int cg_ctas_t(const llb_ctx& c) {
+    return c.variant == 1 ? cg_ctas_v<L, T, 32, 8>(c) : cg_ctas_v<L, T, 64, 4>(c);
+}
+template <class L, class T>
+cudaError_t cg_run_t(const llb_ctx& c, const void* in, void* out) {
+    return c.variant == 1 ? cg_run_v<L, T, 32, 8>(c, in, out) : cg_run_v<L, T, 64, 4>(c, in, out);
 }
 
 }  // namespace

@@ -579,11 +579,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // the default; the others exist for tuning sweeps (llb_params.variant).
 template <class L, class T, int V>
 struct TmaVariant;
-template <class L> struct TmaVariant<L, float, 0> { using type = TmaCfg<L, float, 32, 8, 4, 2>; };
-template <class L> struct TmaVariant<L, float, 1> { using type = TmaCfg<L, float, 32, 8, 3, 3>; };
-template <class L> struct TmaVariant<L, float, 2> { using type = TmaCfg<L, float, 32, 16, 3, 1>; };
-template <class L> struct TmaVariant<L, float, 3> { using type = TmaCfg<L, float, 64, 8, 3, 1>; };
-template <class L> struct TmaVariant<L, float, 4> { using type = TmaCfg<L, float, 64, 4, 4, 2>; };
+template <class L> struct TmaVariant<L, float, 0> { using type = TmaCfg<L, float, 64, 4, 4, 2>; };
+template <class L> struct TmaVariant<L, float, 1> { using type = TmaCfg<L, float, 64, 8, 3, 1>; };
+template <class L> struct TmaVariant<L, float, 2> { using type = TmaCfg<L, float, 96, 4, 3, 1>; };
+template <class L> struct TmaVariant<L, float, 3> { using type = TmaCfg<L, float, 32, 8, 4, 2>; };
+template <class L> struct TmaVariant<L, float, 4> { using type = TmaCfg<L, float, 128, 4, 3, 1>; };
 template <class L, int V> struct TmaVariant<L, double, V> { using type = TmaCfg<L, double, 32, 8, 2, 1>; };
 constexpr int kTmaVariants = 5;
 
@@ -601,11 +601,11 @@ template <int BX_, int BY_, int MINB_>
 struct TiledShape {
     static constexpr int BX = BX_, BY = BY_, MINB = MINB_;
 };
-template <class T, int V> struct TiledVariant { using type = TiledShape<32, 8, 2>; };
-template <> struct TiledVariant<float, 1> { using type = TiledShape<32, 8, 3>; };
-template <> struct TiledVariant<float, 2> { using type = TiledShape<32, 16, 1>; };
-template <> struct TiledVariant<float, 3> { using type = TiledShape<64, 4, 2>; };
-template <> struct TiledVariant<float, 4> { using type = TiledShape<32, 4, 4>; };
+template <class T, int V> struct TiledVariant { using type = TiledShape<64, 4, 2>; };
+template <> struct TiledVariant<float, 1> { using type = TiledShape<64, 8, 1>; };
+template <> struct TiledVariant<float, 2> { using type = TiledShape<96, 4, 1>; };
+template <> struct TiledVariant<float, 3> { using type = TiledShape<32, 8, 2>; };
+template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1>; };
 template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
 
 template <class L, class T, class S>

@@ -87,18 +87,24 @@ def test_ragged_shapes_random_moments_fp64(shape, q, kernel):
     assert_groups(got, ref, 1e-12, what=f"{shape} D3Q{q}")
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@functools.lru_cache(maxsize=None)
+def _oracle_ragged(q):
+    rho, u = inputs.taylor_green_3d(133, 37, 29, u0=0.05, noise=1e-3, seed=7)
+    return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [llb.LLB_KERNEL_TMA, llb.LLB_KERNEL_TILED], ids=["tma", "tiled"])
 @pytest.mark.parametrize("q", [19, 27])
-def test_tma_variants_match_oracle(variant, q):
-    """Every tuning variant of the TMA kernel (tile shape, ring depth, CTAs/SM)
-    computes the same step: ragged multi-tile box, FP32, 1e-5 after 20 steps."""
+def test_kernel_variants_match_oracle(variant, kernel, q):
+    """Every tuning variant of the z-marching kernels (tile shape, ring depth,
+    CTAs/SM) computes the same step: ragged multi-tile box, FP32, 1e-5 after
+    20 steps."""
     shape = (133, 37, 29)
     rho, u = inputs.taylor_green_3d(*shape, u0=0.05, noise=1e-3, seed=7)
-    ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
-    got, used = run_gpu(shape, q, 0.7, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA,
-                        variant=variant)
-    assert used == llb.LLB_KERNEL_TMA
-    assert_groups(got, ref, 1e-5, what=f"variant {variant}")
+    got, used = run_gpu(shape, q, 0.7, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=kernel, variant=variant)
+    assert used == kernel
+    assert_groups(got, _oracle_ragged(q), 1e-5, what=f"variant {variant}")
 
 
 @pytest.mark.parametrize("q", [19, 27])

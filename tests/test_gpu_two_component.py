@@ -60,6 +60,17 @@ def test_droplet_pair_fp64(q, A_h):
 
 
 @pytest.mark.parametrize("q", [19, 27])
+def test_tile_variant_32x8(q):
+    """The 32 x 8 tile variant computes the same step as the default 64 x 4 one."""
+    shape, steps, tau = (40, 24, 20), 20, 0.9
+    ref = _oracle_pair(q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, 0.01, 1e-8)
+    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.01, h_c=3, g_min=1e-8)
+    got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, variant=1, **_params(prm, llb.LLB_F64))
+    assert_groups(got, ref, 1e-12, GROUPS_2, what=f"D3Q{q} 32x8")
+
+
+@pytest.mark.parametrize("q", [19, 27])
 def test_droplet_pair_fp32(q):
     """Same pair without the near-contact decision, FP32 storage, 100 steps: 1e-5."""
     shape, steps, tau = (40, 24, 20), 100, 0.9
