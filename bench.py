@@ -438,7 +438,7 @@ def main():
     if rank != 0:
         return
     nodes = NX * NY * NZ
-    traffic = ncu_traffic("moment_tma_d3q19_f32")
+    traffic = ncu_traffic("moment_tiled_d3q19_f32")
     roof = {"bound": "hbm", "achieved": main_r["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": main_r["achieved_gbs"] / peak, "traffic": traffic,
             "peak_source": peak_src + ", burst copy figure (the step kernel is timed alone)",

@@ -64,6 +64,12 @@ extern "C" {
 /* ---- element types (storage on the device, and host/device buffers) -- */
 #define LLB_F64 0   /* double                                              */
 #define LLB_F32 1   /* float                                               */
+/* 16-bit storage of the one-component moment-only state (llb_params.storage
+ * only; host and device buffers crossing the ABI are LLB_F64 or LLB_F32).
+ * The shifted moments d = rho - 1, j, A = P - cs^2 rho I are stored scaled
+ * by 2^6, 2^4 and 2^10 and all arithmetic is FP32.                        */
+#define LLB_F16S  2 /* IEEE binary16                                       */
+#define LLB_BF16S 3 /* bfloat16                                            */
 
 /* ---- schemes --------------------------------------------------------- */
 /* The moment-only scheme of the paper (Sec. II-III A). */
@@ -86,7 +92,7 @@ typedef struct llb_ctx llb_ctx;
 
 typedef struct llb_params {
     int ncomp;        /* 1 (default) or 2 components                         */
-    int storage;      /* LLB_F32 (default) or LLB_F64                        */
+    int storage;      /* LLB_F32 (default), LLB_F64, LLB_F16S, LLB_BF16S     */
     int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
     int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
     int variant;      /* tile/pipeline variant of the TMA and tiled kernels,

@@ -14,7 +14,9 @@
 
 namespace llb {
 
-size_t elem_size(int dtype) { return dtype == LLB_F64 ? 8 : dtype == LLB_F32 ? 4 : 0; }
+size_t elem_size(int dtype) {
+    return dtype == LLB_F64 ? 8 : dtype == LLB_F32 ? 4 : (dtype == LLB_F16S || dtype == LLB_BF16S) ? 2 : 0;
+}
 
 int canonical_fields(const llb_ctx& c) { return c.ncomp == 2 ? 11 : 10; }
 
@@ -62,7 +64,11 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     if (lattice != 19 && lattice != 27) { *why = "lattice must be 19 or 27"; return LLB_EINVAL; }
     if (!(tau > 0.5) || !std::isfinite(tau)) { *why = "tau must be finite and > 1/2 (nu = cs^2 (tau - 1/2) > 0)"; return LLB_EINVAL; }
     if (p.ncomp != 1 && p.ncomp != 2) { *why = "ncomp must be 1 or 2"; return LLB_EINVAL; }
-    if (!dtype_ok(p.storage)) { *why = "storage must be LLB_F32 or LLB_F64"; return LLB_EINVAL; }
+    const bool narrow = p.storage == LLB_F16S || p.storage == LLB_BF16S;
+    if (!dtype_ok(p.storage) && !narrow) { *why = "storage must be LLB_F32, LLB_F64, LLB_F16S or LLB_BF16S"; return LLB_EINVAL; }
+    if (narrow && (p.ncomp != 1 || p.scheme != LLB_SCHEME_MOMENT)) {
+        *why = "16-bit storage is for the one-component moment-only state"; return LLB_EINVAL;
+    }
     if (p.scheme != LLB_SCHEME_MOMENT && p.scheme != LLB_SCHEME_POPULATION && p.scheme != LLB_SCHEME_POPULATION_BGK) {
         *why = "unknown scheme"; return LLB_EINVAL;
     }
@@ -276,8 +282,9 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
         const int want = c->kernel;
         if (want == LLB_KERNEL_TMA && c->tma_ctas <= 0) return bail(LLB_EINVAL);
         if (want == LLB_KERNEL_TILED && c->tile_ctas <= 0) return bail(LLB_EINVAL);
+        // measured on GB300: the plain-load tiled kernel is the fastest, the TMA-staged one next
         if (want == LLB_KERNEL_AUTO)
-            c->kernel = c->tma_ctas > 0 ? LLB_KERNEL_TMA : c->tile_ctas > 0 ? LLB_KERNEL_TILED : LLB_KERNEL_DIRECT;
+            c->kernel = c->tile_ctas > 0 ? LLB_KERNEL_TILED : c->tma_ctas > 0 ? LLB_KERNEL_TMA : LLB_KERNEL_DIRECT;
     } else {
         c->kernel = LLB_KERNEL_DIRECT;
     }

@@ -15,6 +15,7 @@
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
+#include "storage.cuh"
 
 namespace llb {
 namespace {
@@ -47,7 +48,7 @@ __device__ __forceinline__ void put(T* __restrict__ st, const Layout& L, int x, 
     for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
         const size_t j = L.at(gx, gy, z);
 #pragma unroll
-        for (int f = 0; f < 10; ++f) st[f * L.fs + j] = (T)v[f];
+        for (int f = 0; f < 10; ++f) st[f * L.fs + j] = to_store<T>(v[f], f);
     });
 }
 
@@ -79,11 +80,11 @@ __global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ 
         int x, y, z;
         decode(L, i, x, y, z);
         const size_t j = L.at(x, y, z);
-        const double rho = 1.0 + (double)st[j];
+        const double rho = 1.0 + rd_field(st[j], 0);
         wrt(canon, i, cdt, rho);
-        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
-        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j] + kCs2 * rho);
-        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, (double)st[f * L.fs + j]);
+        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f));
+        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f) + kCs2 * rho);
+        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f));
     }
 }
 
@@ -179,6 +180,15 @@ int grid_for(const llb_ctx& c) {
 }  // namespace
 
 cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int cdt, void* st, int* bad) {
+    if (c.storage == LLB_F16S) {
+        k_canon_to_shifted<__half><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<__half*>(st), c.lay, bad);
+        return cudaGetLastError();
+    }
+    if (c.storage == LLB_BF16S) {
+        k_canon_to_shifted<__nv_bfloat16><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<__nv_bfloat16*>(st),
+                                                                             c.lay, bad);
+        return cudaGetLastError();
+    }
     if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
             k_canon_to_shifted2<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
@@ -194,6 +204,15 @@ cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int
 }
 
 cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* canon, int cdt) {
+    if (c.storage == LLB_F16S) {
+        k_shifted_to_canon<__half><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const __half*>(st), canon, cdt, c.lay);
+        return cudaGetLastError();
+    }
+    if (c.storage == LLB_BF16S) {
+        k_shifted_to_canon<__nv_bfloat16><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const __nv_bfloat16*>(st), canon,
+                                                                             cdt, c.lay);
+        return cudaGetLastError();
+    }
     if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
             k_shifted_to_canon2<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
@@ -209,6 +228,15 @@ cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* 
 }
 
 cudaError_t launch_equilibrium(const llb_ctx& c, const void* rho, const void* u, int dt, void* st, int* bad) {
+    if (c.storage == LLB_F16S) {
+        k_equilibrium<__half><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<__half*>(st), c.lay, bad);
+        return cudaGetLastError();
+    }
+    if (c.storage == LLB_BF16S) {
+        k_equilibrium<__nv_bfloat16><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<__nv_bfloat16*>(st),
+                                                                        c.lay, bad);
+        return cudaGetLastError();
+    }
     if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
             k_equilibrium2<double><<<grid_for(c), 256, 0, c.stream>>>(rho, u, dt, static_cast<double*>(st), c.lay, bad);

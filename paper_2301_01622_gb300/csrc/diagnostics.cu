@@ -15,6 +15,7 @@
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
+#include "storage.cuh"
 
 namespace llb {
 namespace {
@@ -84,10 +85,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
         const int x = (int)(n % L.nx);
         const size_t r = n / L.nx;
         const size_t i = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
-        const double d = (double)m[o * F + i];
-        const double jx = (double)m[(o + 1) * F + i], jy = (double)m[(o + 2) * F + i], jz = (double)m[(o + 3) * F + i];
+        const double d = rd_field(m[o * F + i], 0);
+        const double jx = rd_field(m[(o + 1) * F + i], 1), jy = rd_field(m[(o + 2) * F + i], 2),
+                     jz = rd_field(m[(o + 3) * F + i], 3);
         const double rho = 1.0 + d;
-        const double drop = NC == 2 ? (double)m[i] : rho;
+        const double drop = NC == 2 ? rd_field(m[i], 0) : rho;
         p.v[0] += d;
         p.v[1] += jx;
         p.v[2] += jy;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
         if (NC == 2) p.v[8] += drop;
         bool finite = isfinite(d) && isfinite(jx) && isfinite(jy) && isfinite(jz) && isfinite(drop);
 #pragma unroll
-        for (int f = o + 4; f < o + 10; ++f) finite = finite && isfinite((double)m[f * F + i]);
+        for (int f = o + 4; f < o + 10; ++f) finite = finite && isfinite(rd_field(m[f * F + i], f - o));
         if (!finite) p.v[7] = 1.0;
     }
     p = block_reduce(p);
@@ -150,7 +152,12 @@ int diag_blocks(const llb_ctx& c) {
 cudaError_t launch_diagnostics(const llb_ctx& c, const void* mom, void* scratch, llb_diag* dev_out) {
     const int nb = diag_blocks(c);
     double* rows = static_cast<double*>(scratch);
-    if (c.ncomp == 2) {
+    if (c.storage == LLB_F16S)
+        k_diag_partial<__half, 1><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const __half*>(mom), c.lay, rows);
+    else if (c.storage == LLB_BF16S)
+        k_diag_partial<__nv_bfloat16, 1><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const __nv_bfloat16*>(mom),
+                                                                             c.lay, rows);
+    else if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
             k_diag_partial<double, 2><<<nb, kDiagThreads, 0, c.stream>>>(static_cast<const double*>(mom), c.lay, rows);
         else

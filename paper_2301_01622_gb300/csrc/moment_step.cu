@@ -35,6 +35,7 @@
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
+#include "storage.cuh"
 #include "tma.cuh"
 
 namespace llb {
@@ -42,39 +43,40 @@ namespace {
 
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) before a TMA wait gives up
 
-template <class T>
-__device__ __forceinline__ Mom<T> load_mom(const T* __restrict__ p, size_t idx, size_t fs) {
+// Ten shifted moments of node idx from a state of element type S (converted to T).
+template <class T, class S>
+__device__ __forceinline__ Mom<T> load_mom(const S* __restrict__ p, size_t idx, size_t fs) {
     Mom<T> m;
-    m.d = __ldg(p + idx);
-    m.jx = __ldg(p + fs + idx);
-    m.jy = __ldg(p + 2 * fs + idx);
-    m.jz = __ldg(p + 3 * fs + idx);
-    m.axx = __ldg(p + 4 * fs + idx);
-    m.ayy = __ldg(p + 5 * fs + idx);
-    m.azz = __ldg(p + 6 * fs + idx);
-    m.axy = __ldg(p + 7 * fs + idx);
-    m.axz = __ldg(p + 8 * fs + idx);
-    m.ayz = __ldg(p + 9 * fs + idx);
+    m.d = ld_field<T>(p + idx, 0);
+    m.jx = ld_field<T>(p + fs + idx, 1);
+    m.jy = ld_field<T>(p + 2 * fs + idx, 2);
+    m.jz = ld_field<T>(p + 3 * fs + idx, 3);
+    m.axx = ld_field<T>(p + 4 * fs + idx, 4);
+    m.ayy = ld_field<T>(p + 5 * fs + idx, 5);
+    m.azz = ld_field<T>(p + 6 * fs + idx, 6);
+    m.axy = ld_field<T>(p + 7 * fs + idx, 7);
+    m.axz = ld_field<T>(p + 8 * fs + idx, 8);
+    m.ayz = ld_field<T>(p + 9 * fs + idx, 9);
     return m;
 }
 
-template <class T>
-__device__ __forceinline__ void store_mom(T* __restrict__ p, size_t idx, size_t fs, const Mom<T>& m) {
-    p[idx] = m.d;
-    p[fs + idx] = m.jx;
-    p[2 * fs + idx] = m.jy;
-    p[3 * fs + idx] = m.jz;
-    p[4 * fs + idx] = m.axx;
-    p[5 * fs + idx] = m.ayy;
-    p[6 * fs + idx] = m.azz;
-    p[7 * fs + idx] = m.axy;
-    p[8 * fs + idx] = m.axz;
-    p[9 * fs + idx] = m.ayz;
+template <class T, class S>
+__device__ __forceinline__ void store_mom(S* __restrict__ p, size_t idx, size_t fs, const Mom<T>& m) {
+    p[idx] = to_store<S>(m.d, 0);
+    p[fs + idx] = to_store<S>(m.jx, 1);
+    p[2 * fs + idx] = to_store<S>(m.jy, 2);
+    p[3 * fs + idx] = to_store<S>(m.jz, 3);
+    p[4 * fs + idx] = to_store<S>(m.axx, 4);
+    p[5 * fs + idx] = to_store<S>(m.ayy, 5);
+    p[6 * fs + idx] = to_store<S>(m.azz, 6);
+    p[7 * fs + idx] = to_store<S>(m.axy, 7);
+    p[8 * fs + idx] = to_store<S>(m.axz, 8);
+    p[9 * fs + idx] = to_store<S>(m.ayz, 9);
 }
 
 // Store node (x, y, z) and its periodic ghost copies.
-template <class T>
-__device__ __forceinline__ void store_node(T* __restrict__ p, const Layout& L, int x, int y, int z, const Mom<T>& m) {
+template <class T, class S>
+__device__ __forceinline__ void store_node(S* __restrict__ p, const Layout& L, int x, int y, int z, const Mom<T>& m) {
     for_node_and_ghosts(L, x, y, [&](int gx, int gy) { store_mom(p, L.at(gx, gy, z), L.fs, m); });
 }
 
@@ -129,8 +131,8 @@ Sched plan(int nx, int ny, int nz, int BX, int BY, int grid) {
 
 // ---------------------------------------------------------------------------
 // Direct kernel: grid (ceil(nx/128), ny, nz), one thread per output node.
-template <class L, class T>
-__global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in, T* __restrict__ out, Layout lay,
+template <class L, class T, class S>
+__global__ void __launch_bounds__(128) k_moment_direct(const S* __restrict__ in, S* __restrict__ out, Layout lay,
                                                        T omega) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(128) k_moment_direct(const T* __restrict__ in,
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
                 const size_t s = lay.at(wrap_idx(x - cx, lay.nx), wrap_idx(y - cy, lay.ny), wrap_idx(z - cz, lay.nz));
-                const Mom<T> c = collide(load_mom(in, s, lay.fs), omega);
+                const Mom<T> c = collide(load_mom<T>(in, s, lay.fs), omega);
                 acc.add(g_dir<L, T>(c, g_shared(c), cx, cy, cz), cx, cy, cz);
             }
     store_node(out, lay, x, y, z, acc.finish());
@@ -349,9 +351,9 @@ struct Tiled {
     static_assert(NH <= NT, "halo must fit one node per thread");
 };
 
-template <class L, class T, int BX, int BY, int MINB>
+template <class L, class T, int BX, int BY, int MINB, class S>
 __global__ void __launch_bounds__(BX * BY, MINB)
-    k_moment_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, T omega, Sched sc) {
+    k_moment_tiled(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc) {
     using K = Tiled<L, T, BX, BY>;
     constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -376,9 +378,9 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
 
         int zs = pmod(za - 1, nz);
-        Mom<T> m1 = load_mom(in, zs * plane + off1, lay.fs);
+        Mom<T> m1 = load_mom<T>(in, zs * plane + off1, lay.fs);
         Mom<T> m2 = m1;
-        if (has2) m2 = load_mom(in, zs * plane + off2, lay.fs);
+        if (has2) m2 = load_mom<T>(in, zs * plane + off2, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
@@ -389,8 +391,8 @@ __global__ void __launch_bounds__(BX * BY, MINB)
             const bool more = s + 1 <= zb;
             if (more) {
                 const size_t zo = (size_t)pmod(s + 1, nz) * plane;
-                p1 = load_mom(in, zo + off1, lay.fs);
-                if (has2) p2 = load_mom(in, zo + off2, lay.fs);
+                p1 = load_mom<T>(in, zo + off1, lay.fs);
+                if (has2) p2 = load_mom<T>(in, zo + off2, lay.fs);
             }
             const Mom<T> c1 = collide(m1, omega);
             publish<L, T, HN>(G, n1, c1);
@@ -587,11 +589,11 @@ template <class L> struct TmaVariant<L, float, 4> { using type = TmaCfg<L, float
 template <class L, int V> struct TmaVariant<L, double, V> { using type = TmaCfg<L, double, 32, 8, 2, 1>; };
 constexpr int kTmaVariants = 5;
 
-template <class L, class T>
+template <class L, class T, class S>
 cudaError_t run_direct(const llb_ctx& c, const void* in, void* out) {
     dim3 block(128), grid((c.nx + 127) / 128, c.ny, c.nz);
-    k_moment_direct<L, T><<<grid, block, 0, c.stream>>>(static_cast<const T*>(in), static_cast<T*>(out), c.lay,
-                                                         (T)c.omega);
+    k_moment_direct<L, T, S><<<grid, block, 0, c.stream>>>(static_cast<const S*>(in), static_cast<S*>(out), c.lay,
+                                                            (T)c.omega);
     return cudaGetLastError();
 }
 
@@ -608,10 +610,10 @@ template <> struct TiledVariant<float, 3> { using type = TiledShape<32, 8, 2>; }
 template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1>; };
 template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
 
-template <class L, class T, class S>
+template <class L, class T, class St, class S>
 int tiled_ctas_c(const llb_ctx& c) {
     using K = Tiled<L, T, S::BX, S::BY>;
-    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB>;
+    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB, St>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
@@ -622,28 +624,28 @@ int tiled_ctas_c(const llb_ctx& c) {
     return std::min(sc.nitems, per_sm * c.num_sms);
 }
 
-template <class L, class T, class S>
+template <class L, class T, class St, class S>
 cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
     using K = Tiled<L, T, S::BX, S::BY>;
     const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
     const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, grid);
-    k_moment_tiled<L, T, S::BX, S::BY, S::MINB><<<grid, K::NT, K::smem_bytes, c.stream>>>(
-        static_cast<const T*>(in), static_cast<T*>(out), c.lay, (T)c.omega, sc);
+    k_moment_tiled<L, T, S::BX, S::BY, S::MINB, St><<<grid, K::NT, K::smem_bytes, c.stream>>>(
+        static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc);
     return cudaGetLastError();
 }
 
 #define LLB_TILED_VARIANT(fn, ...)                                                           \
     switch (c.variant) {                                                                     \
-        case 1: return fn<L, T, typename TiledVariant<T, 1>::type>(__VA_ARGS__);             \
-        case 2: return fn<L, T, typename TiledVariant<T, 2>::type>(__VA_ARGS__);             \
-        case 3: return fn<L, T, typename TiledVariant<T, 3>::type>(__VA_ARGS__);             \
-        case 4: return fn<L, T, typename TiledVariant<T, 4>::type>(__VA_ARGS__);             \
-        default: return fn<L, T, typename TiledVariant<T, 0>::type>(__VA_ARGS__);            \
+        case 1: return fn<L, T, St, typename TiledVariant<T, 1>::type>(__VA_ARGS__);         \
+        case 2: return fn<L, T, St, typename TiledVariant<T, 2>::type>(__VA_ARGS__);         \
+        case 3: return fn<L, T, St, typename TiledVariant<T, 3>::type>(__VA_ARGS__);         \
+        case 4: return fn<L, T, St, typename TiledVariant<T, 4>::type>(__VA_ARGS__);         \
+        default: return fn<L, T, St, typename TiledVariant<T, 0>::type>(__VA_ARGS__);        \
     }
 
-template <class L, class T>
+template <class L, class T, class St>
 int tiled_ctas(const llb_ctx& c) { LLB_TILED_VARIANT(tiled_ctas_c, c) }
-template <class L, class T>
+template <class L, class T, class St>
 cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) { LLB_TILED_VARIANT(run_tiled_c, c, in, out) }
 
 template <class L, class T, class C>
@@ -709,23 +711,40 @@ bool tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) { LLB_TMA_VARIANT
 
 }  // namespace
 
-#define LLB_MDISPATCH(fn, ...)                                                                       \
-    (c.Q == 19 ? (c.storage == LLB_F64 ? fn<D3Q19, double>(__VA_ARGS__) : fn<D3Q19, float>(__VA_ARGS__)) \
-               : (c.storage == LLB_F64 ? fn<D3Q27, double>(__VA_ARGS__) : fn<D3Q27, float>(__VA_ARGS__)))
+// (lattice, element type) -> kernel instance.  16-bit states compute in FP32.
+#define LLB_SDISPATCH(fn, ...)                                                                    \
+    switch (c.storage) {                                                                          \
+        case LLB_F64: return c.Q == 19 ? fn<D3Q19, double, double>(__VA_ARGS__)                   \
+                                       : fn<D3Q27, double, double>(__VA_ARGS__);                  \
+        case LLB_F16S: return c.Q == 19 ? fn<D3Q19, float, __half>(__VA_ARGS__)                   \
+                                        : fn<D3Q27, float, __half>(__VA_ARGS__);                  \
+        case LLB_BF16S: return c.Q == 19 ? fn<D3Q19, float, __nv_bfloat16>(__VA_ARGS__)           \
+                                         : fn<D3Q27, float, __nv_bfloat16>(__VA_ARGS__);          \
+        default: return c.Q == 19 ? fn<D3Q19, float, float>(__VA_ARGS__)                          \
+                                  : fn<D3Q27, float, float>(__VA_ARGS__);                         \
+    }
+
+// The TMA kernel stages FP32 or FP64 boxes only.
+#define LLB_MDISPATCH(fn, fallback, ...)                                                          \
+    switch (c.storage) {                                                                          \
+        case LLB_F64: return c.Q == 19 ? fn<D3Q19, double>(__VA_ARGS__) : fn<D3Q27, double>(__VA_ARGS__); \
+        case LLB_F32: return c.Q == 19 ? fn<D3Q19, float>(__VA_ARGS__) : fn<D3Q27, float>(__VA_ARGS__);   \
+        default: return fallback;                                                                 \
+    }
 
 cudaError_t launch_moment_direct(const llb_ctx& c, const void* in, void* out) {
-    return LLB_MDISPATCH(run_direct, c, in, out);
+    LLB_SDISPATCH(run_direct, c, in, out)
 }
-int moment_tiled_ctas(const llb_ctx& c) { return LLB_MDISPATCH(tiled_ctas, c); }
+int moment_tiled_ctas(const llb_ctx& c) { LLB_SDISPATCH(tiled_ctas, c) }
 cudaError_t launch_moment_tiled(const llb_ctx& c, const void* in, void* out) {
-    return LLB_MDISPATCH(run_tiled, c, in, out);
+    LLB_SDISPATCH(run_tiled, c, in, out)
 }
-int moment_tma_ctas(const llb_ctx& c) { return LLB_MDISPATCH(tma_ctas, c); }
+int moment_tma_ctas(const llb_ctx& c) { LLB_MDISPATCH(tma_ctas, 0, c) }
 cudaError_t launch_moment_tma(const llb_ctx& c, int in_index, void* out) {
-    return LLB_MDISPATCH(run_tma, c, in_index, out);
+    LLB_MDISPATCH(run_tma, cudaErrorInvalidValue, c, in_index, out)
 }
 bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
-    return LLB_MDISPATCH(tma_encode, c, buf, out);
+    LLB_MDISPATCH(tma_encode, false, c, buf, out)
 }
 
 }  // namespace llb

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libllb.so")
 
 LLB_OK, LLB_EINVAL, LLB_ENOMEM, LLB_ECUDA, LLB_EUNSTABLE, LLB_ETIMEOUT, LLB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-LLB_F64, LLB_F32 = 0, 1
+LLB_F64, LLB_F32, LLB_F16S, LLB_BF16S = 0, 1, 2, 3
 LLB_SCHEME_MOMENT, LLB_SCHEME_POPULATION, LLB_SCHEME_POPULATION_BGK = 0, 1, 2
 LLB_KERNEL_AUTO, LLB_KERNEL_DIRECT, LLB_KERNEL_TILED, LLB_KERNEL_TMA = 0, 1, 2, 3
 LLB_FLAG_NONFINITE, LLB_FLAG_NONPOSITIVE = 1, 2

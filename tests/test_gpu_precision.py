@@ -1,0 +1,63 @@
+"""Reduced-precision storage (16-bit shifted and scaled moments, FP32
+arithmetic) against the FP64 oracle.  The bounds are measured errors of this
+implementation rounded up, stated per moment group (rho; j; P) as
+max |gpu - oracle| / max |oracle| over the group after 200 steps of the 32^3
+Taylor-Green vortex (u0 = 0.05, tau = 0.8), and after one step of the full
+256^3 bench field."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import D3Q19, D3Q27, lb
+from paper_2301_01622_gb300 import inputs, llb
+
+from gpu_helpers import group_errors, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+LAT = {19: D3Q19, 27: D3Q27}
+# measured on GB300 (see the test log), rounded up by about 2x
+BOUNDS = {
+    llb.LLB_F16S: {"rho": 2e-6, "j": 2e-2, "P": 2e-5},
+    llb.LLB_BF16S: {"rho": 2e-5, "j": 2e-1, "P": 2e-4},
+}
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(q):
+    rho, u = inputs.taylor_green_3d(32, 32, 32, u0=0.05)
+    return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.8, 200)
+
+
+@pytest.mark.parametrize("storage", [llb.LLB_F16S, llb.LLB_BF16S], ids=["f16", "bf16"])
+@pytest.mark.parametrize("q", [19, 27])
+def test_taylor_green_200_steps(storage, q):
+    rho, u = inputs.taylor_green_3d(32, 32, 32, u0=0.05)
+    got, used = run_gpu((32, 32, 32), q, 0.8, 200, rho=rho, u=u, storage=storage)
+    assert used == llb.LLB_KERNEL_TILED
+    errs = group_errors(got, _oracle(q))
+    print("storage", storage, "D3Q", q, errs)
+    for k, v in errs.items():
+        assert v <= BOUNDS[storage][k], (k, v)
+
+
+@pytest.mark.parametrize("storage", [llb.LLB_F16S, llb.LLB_BF16S], ids=["f16", "bf16"])
+def test_direct_kernel_agrees(storage):
+    """The direct kernel reads and writes the same 16-bit format."""
+    rho, u = inputs.taylor_green_3d(24, 20, 16, u0=0.05, noise=1e-3)
+    a, _ = run_gpu((24, 20, 16), 19, 0.7, 10, rho=rho, u=u, storage=storage, kernel=llb.LLB_KERNEL_DIRECT)
+    b, _ = run_gpu((24, 20, 16), 19, 0.7, 10, rho=rho, u=u, storage=storage, kernel=llb.LLB_KERNEL_TILED)
+    ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), D3Q19, 0.7, 10)
+    for got in (a, b):
+        errs = group_errors(got, ref)
+        for k, v in errs.items():
+            assert v <= BOUNDS[storage][k], (k, v)
+
+
+def test_narrow_storage_rejected_where_unsupported():
+    for kw in ({"ncomp": 2}, {"scheme": llb.LLB_SCHEME_POPULATION}):
+        with pytest.raises(llb.LLBError):
+            llb.llb_create(16, 16, 16, 19, 0.8, llb.llb_params_default(storage=llb.LLB_F16S, **kw))
+    with pytest.raises(llb.LLBError):
+        llb.llb_create(64, 64, 64, 19, 0.8, llb.llb_params_default(storage=llb.LLB_F16S, kernel=llb.LLB_KERNEL_TMA))
