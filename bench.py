@@ -173,7 +173,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("moment_step.cu", "lattice.cuh"):
+    for f in ("moment_step.cu", "lattice.cuh", "layout.cuh", "storage.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2301_01622_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -178,6 +178,20 @@ LLB_API int llb_init_equilibrium(llb_ctx* ctx, const void* host_rho, const void*
 /* Advance nsteps >= 0 time steps (asynchronous on the context stream). */
 LLB_API int llb_step(llb_ctx* ctx, int nsteps);
 
+/* Same as llb_step, replayed from a CUDA graph: the first call for a given
+ * nsteps (and flip-flop parity) captures the nsteps launches into a graph on
+ * a private stream; later calls launch that graph on the context stream.
+ * Saves the per-launch host overhead of long runs of short steps. */
+LLB_API int llb_step_graph(llb_ctx* ctx, int nsteps);
+
+/* Autotuner: times every kernel and tile/pipeline variant that can run this
+ * context's shape (tiled, TMA, direct; `trials` launches each), keeps the
+ * fastest and reports it through kernel/variant (either may be NULL).  The
+ * state does not advance: each trial recomputes the current step into the
+ * spare flip-flop copy.  Synchronises.  Population schemes are left as they
+ * are. */
+LLB_API int llb_autotune(llb_ctx* ctx, int trials, int* kernel, int* variant);
+
 /* Copy the current canonical moments into caller HOST memory of element
  * type host_dtype.  Synchronises the stream. */
 LLB_API int llb_get_moments(llb_ctx* ctx, void* host_out, int host_dtype);

@@ -174,6 +174,49 @@ int check_bad_flag(llb_ctx* c) {
     return LLB_OK;
 }
 
+// Launch one step from buffer `cur` into the other copy, without flipping.
+cudaError_t launch_one(llb_ctx* c, int cur) {
+    const void* in = c->buf[cur];
+    void* out = c->buf[1 - cur];
+    if (c->ncomp == 2) return launch_cg_tiled(*c, in, out);
+    if (c->scheme == LLB_SCHEME_MOMENT)
+        return c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, cur, out)
+               : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
+                                               : launch_moment_direct(*c, in, out);
+    return launch_population_step(*c, in, out, c->scheme == LLB_SCHEME_POPULATION_BGK);
+}
+
+// Prepare the launch plan of (kernel, variant); false if it cannot run this shape.
+bool configure(llb_ctx* c, int kernel, int variant) {
+    c->kernel = kernel;
+    c->variant = variant;
+    if (c->ncomp == 2) {
+        c->tile_ctas = cg_tiled_ctas(*c);
+        cudaGetLastError();
+        return kernel == LLB_KERNEL_TILED && c->tile_ctas > 0;
+    }
+    if (kernel == LLB_KERNEL_TILED) {
+        c->tile_ctas = moment_tiled_ctas(*c);
+        cudaGetLastError();
+        return c->tile_ctas > 0;
+    }
+    if (kernel == LLB_KERNEL_TMA) {
+        c->tmap_ok = moment_tma_encode(*c, c->buf[0], &c->tmap[0]) && moment_tma_encode(*c, c->buf[1], &c->tmap[1]);
+        c->tma_ctas = c->tmap_ok ? moment_tma_ctas(*c) : 0;
+        cudaGetLastError();
+        return c->tma_ctas > 0;
+    }
+    return kernel == LLB_KERNEL_DIRECT;
+}
+
+void drop_graphs(llb_ctx* c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
+        c->graph_exec[k] = nullptr;
+        c->graph_steps[k] = 0;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -301,6 +344,7 @@ void llb_destroy(llb_ctx* c) {
     if (c->staging) cudaFree(c->staging);
     if (c->diag_scratch) cudaFree(c->diag_scratch);
     if (c->flag_dev) cudaFree(c->flag_dev);
+    drop_graphs(c);
     cudaGetLastError();
     delete c;
 }
@@ -350,21 +394,103 @@ int llb_step(llb_ctx* c, int nsteps) {
     LLB_CHECK_CTX(c);
     if (nsteps < 0) return fail(c, LLB_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
-        const void* in = c->buf[c->cur];
-        void* out = c->buf[1 - c->cur];
-        cudaError_t e;
-        if (c->ncomp == 2)
-            e = launch_cg_tiled(*c, in, out);
-        else if (c->scheme == LLB_SCHEME_MOMENT)
-            e = c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, c->cur, out)
-                : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
-                                                : launch_moment_direct(*c, in, out);
-        else
-            e = launch_population_step(*c, in, out, c->scheme == LLB_SCHEME_POPULATION_BGK);
+        const cudaError_t e = launch_one(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
         c->cur = 1 - c->cur;
         ++c->t;
     }
+    return LLB_OK;
+}
+
+int llb_step_graph(llb_ctx* c, int nsteps) {
+    LLB_CHECK_CTX(c);
+    if (nsteps < 0) return fail(c, LLB_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return LLB_OK;
+    const int k = c->cur;
+    if (!c->graph_exec[k] || c->graph_steps[k] != nsteps) {
+        if (c->graph_exec[k]) {
+            cudaGraphExecDestroy(c->graph_exec[k]);
+            c->graph_exec[k] = nullptr;
+        }
+        // capture on a private stream (the context stream may be the legacy default stream)
+        cudaStream_t cap = nullptr;
+        LLB_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        cudaStream_t saved = c->stream;
+        c->stream = cap;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int cur = k;
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+            e = launch_one(c, cur);
+            cur = 1 - cur;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        c->stream = saved;
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec[k], g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            c->graph_exec[k] = nullptr;
+            return cuda_fail(c, e, "graph capture");
+        }
+        c->graph_steps[k] = nsteps;
+    }
+    LLB_CUDA(c, cudaGraphLaunch(c->graph_exec[k], c->stream), "graph launch");
+    if (nsteps % 2) c->cur = 1 - c->cur;
+    c->t += nsteps;
+    return LLB_OK;
+}
+
+int llb_autotune(llb_ctx* c, int trials, int* kernel, int* variant) {
+    LLB_CHECK_CTX(c);
+    if (trials < 1) return fail(c, LLB_EINVAL, "trials must be >= 1");
+    if (c->scheme != LLB_SCHEME_MOMENT) {
+        if (kernel) *kernel = c->kernel;
+        if (variant) *variant = c->variant;
+        return LLB_OK;
+    }
+    struct Cand { int kernel, variant; };
+    Cand cands[12];
+    int nc = 0;
+    const int nvar = c->ncomp == 2 ? 2 : 5;
+    for (int v = 0; v < nvar; ++v) cands[nc++] = {LLB_KERNEL_TILED, v};
+    if (c->ncomp == 1) {
+        for (int v = 0; v < 5; ++v) cands[nc++] = {LLB_KERNEL_TMA, v};
+        cands[nc++] = {LLB_KERNEL_DIRECT, 0};
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LLB_CUDA(c, cudaEventCreate(&e0), "event");
+    LLB_CUDA(c, cudaEventCreate(&e1), "event");
+    const int keep_k = c->kernel, keep_v = c->variant;
+    float best = -1.0f;
+    Cand win = {keep_k, keep_v};
+    for (int i = 0; i < nc; ++i) {
+        if (!configure(c, cands[i].kernel, cands[i].variant)) continue;
+        // every trial recomputes step t -> t+1 into the spare copy: the state does not move
+        cudaError_t e = launch_one(c, c->cur);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < trials && e == cudaSuccess; ++r) e = launch_one(c, c->cur);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(c, e, "autotune");
+        }
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            win = cands[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!configure(c, win.kernel, win.variant)) configure(c, keep_k, keep_v);
+    drop_graphs(c);
+    if (kernel) *kernel = c->kernel;
+    if (variant) *variant = c->variant;
     return LLB_OK;
 }
 

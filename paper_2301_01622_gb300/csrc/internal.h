@@ -48,6 +48,9 @@ struct llb_ctx {
     // persistent launch plans (grid sizes), 0 = kernel unusable for this shape
     int tile_ctas = 0;
     int tma_ctas = 0;
+    // captured step sequences (llb_step_graph): one per starting flip-flop copy
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    int graph_steps[2] = {0, 0};
 };
 
 namespace llb {

@@ -69,6 +69,8 @@ _SIGS = {
     "llb_init_moments_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "llb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "llb_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "llb_step_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "llb_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "llb_get_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "llb_get_moments_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "llb_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(llb_diag)]),
@@ -205,6 +207,16 @@ def llb_init_equilibrium(ctx, host_rho, host_u):
 
 def llb_step(ctx, nsteps: int = 1):
     _check(lib().llb_step(ctx, int(nsteps)), "llb_step", ctx)
+
+
+def llb_step_graph(ctx, nsteps: int = 1):
+    _check(lib().llb_step_graph(ctx, int(nsteps)), "llb_step_graph", ctx)
+
+
+def llb_autotune(ctx, trials: int = 5):
+    k, v = C.c_int(), C.c_int()
+    _check(lib().llb_autotune(ctx, int(trials), C.byref(k), C.byref(v)), "llb_autotune", ctx)
+    return k.value, v.value
 
 
 def llb_get_moments(ctx, host_out):

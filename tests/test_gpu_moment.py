@@ -23,7 +23,7 @@ KIDS = ["tma", "tiled", "direct"]
 
 
 def tma_fits(shape):
-    """The TMA kernel needs a padded row of >= 40 elements and >= 10 rows (tile 32 x 8 plus halo)."""
+    """The FP64 TMA kernel (tile 32 x 8) needs a padded row of >= 40 elements and >= 10 rows."""
     nx, ny, _ = shape
     return ((nx + 16 + 7) // 8) * 8 >= 40 and ny + 2 >= 10
 
@@ -51,7 +51,10 @@ def test_taylor_green_fp32_200_steps(q, kernel):
     """Same run with FP32 storage and arithmetic: 1e-5 after 200 steps."""
     n, tau = 32, 0.8
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05)
-    got, _ = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F32, kernel=kernel)
+    # the default FP32 TMA tile (64 x 4) is wider than this box; variant 3 is 32 x 8
+    variant = 3 if kernel == llb.LLB_KERNEL_TMA else 0
+    got, used = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F32, kernel=kernel, variant=variant)
+    assert used == kernel
     assert_groups(got, oracle_tg(q, n, tau, 200, 0.0), 1e-5, what=f"D3Q{q} fp32")
 
 
@@ -123,8 +126,8 @@ def test_zero_steps_round_trip(q):
 def test_tiled_is_deterministic_and_matches_direct(q):
     n = 40
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=5)
-    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA)
-    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA)
+    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=3)
+    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=3)
     c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
     d, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
     assert np.array_equal(a, b)
