@@ -238,6 +238,34 @@ LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
  * the context runs (for profiling and zero-copy views). */
 LLB_API int llb_state_device(const llb_ctx* ctx, void** dev_ptr, int* dtype, int* kernel);
 
+/* ---- batched ensembles ----------------------------------------------
+ * Independent two-component boxes of (possibly) different sizes advanced
+ * together: each step is ONE persistent launch whose CTAs walk the work
+ * items of every box.  All boxes share lattice, tau and llb_params
+ * (ncomp must be 2; p->stream is used for every box).  Not in the paper:
+ * it serves ensembles of droplet collisions of the kind the paper's
+ * "many drops" motivation (Sec. III B) calls for. */
+typedef struct llb_batch llb_batch;
+
+/* dims: 3 * ndomains ints, (nx, ny, nz) of each box (each >= 4). */
+LLB_API int llb_batch_create(llb_batch** out, int ndomains, const int* dims, int lattice, double tau,
+                             const llb_params* p);
+/* Releases every box.  NULL-safe. */
+LLB_API void llb_batch_destroy(llb_batch* b);
+/* Borrow the context of box d for llb_init_*, llb_get_moments*,
+ * llb_diagnostics; it stays owned by the batch (llb_step and llb_destroy on
+ * it are refused / ignored). */
+LLB_API int llb_batch_domain(llb_batch* b, int d, llb_ctx** ctx);
+/* Total nodes over all boxes. */
+LLB_API int llb_batch_nodes(const llb_batch* b, long long* nodes);
+/* Advance every box by nsteps (one launch per step; asynchronous). */
+LLB_API int llb_batch_step(llb_batch* b, int nsteps);
+/* Same, replayed from a captured CUDA graph of nsteps launches. */
+LLB_API int llb_batch_step_graph(llb_batch* b, int nsteps);
+/* Time the tile variants (`trials` launches each, state unchanged), keep the
+ * fastest, report it through *variant (may be NULL).  Synchronises. */
+LLB_API int llb_batch_autotune(llb_batch* b, int trials, int* variant);
+
 /* Static strings; never NULL. */
 LLB_API const char* llb_status_string(int status);
 LLB_API const char* llb_last_error(const llb_ctx* ctx);

@@ -337,7 +337,7 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
 }
 
 void llb_destroy(llb_ctx* c) {
-    if (!c) return;
+    if (!c || c->in_batch) return;  // a box of a batch is released by llb_batch_destroy
     cudaStreamSynchronize(c->stream);
     for (int b = 0; b < 2; ++b)
         if (c->owns[b] && c->buf[b]) cudaFree(c->buf[b]);
@@ -392,6 +392,7 @@ int llb_init_equilibrium(llb_ctx* c, const void* host_rho, const void* host_u, i
 
 int llb_step(llb_ctx* c, int nsteps) {
     LLB_CHECK_CTX(c);
+    if (c->in_batch) return fail(c, LLB_EINVAL, "this box belongs to a batch: step it with llb_batch_step");
     if (nsteps < 0) return fail(c, LLB_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
         const cudaError_t e = launch_one(c, c->cur);
@@ -404,6 +405,7 @@ int llb_step(llb_ctx* c, int nsteps) {
 
 int llb_step_graph(llb_ctx* c, int nsteps) {
     LLB_CHECK_CTX(c);
+    if (c->in_batch) return fail(c, LLB_EINVAL, "this box belongs to a batch: step it with llb_batch_step");
     if (nsteps < 0) return fail(c, LLB_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return LLB_OK;
     const int k = c->cur;
@@ -444,6 +446,7 @@ int llb_step_graph(llb_ctx* c, int nsteps) {
 
 int llb_autotune(llb_ctx* c, int trials, int* kernel, int* variant) {
     LLB_CHECK_CTX(c);
+    if (c->in_batch) return fail(c, LLB_EINVAL, "this box belongs to a batch: step it with llb_batch_step");
     if (trials < 1) return fail(c, LLB_EINVAL, "trials must be >= 1");
     if (c->scheme != LLB_SCHEME_MOMENT) {
         if (kernel) *kernel = c->kernel;

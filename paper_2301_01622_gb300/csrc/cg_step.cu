@@ -94,6 +94,21 @@ __device__ __forceinline__ void store_node2(T* __restrict__ p, const Layout& L, 
 }
 
 template <class T>
+__device__ __forceinline__ void store_node2_at(T* __restrict__ p, size_t fs, T r1, const Mom<T>& m) {
+    p[0] = r1;
+    p[fs] = m.d;
+    p[2 * fs] = m.jx;
+    p[3 * fs] = m.jy;
+    p[4 * fs] = m.jz;
+    p[5 * fs] = m.axx;
+    p[6 * fs] = m.ayy;
+    p[7 * fs] = m.azz;
+    p[8 * fs] = m.axy;
+    p[9 * fs] = m.axz;
+    p[10 * fs] = m.ayz;
+}
+
+template <class T>
 __device__ __forceinline__ T phi_of(T r1, T d) {
     return T(2) * r1 / (T(1) + d) - T(1);
 }
@@ -335,6 +350,7 @@ __device__ __forceinline__ int halo_role2(int t, int& hx, int& hy) {
 struct Sched2 {
     int ncx, ntiles, zc, nitems;
 };
+static_assert(sizeof(Sched2) == 4 * sizeof(int), "schedule layout");
 
 template <class L, class T, int BX, int BY>
 struct CGCfg {
@@ -348,9 +364,11 @@ struct CGCfg {
     static_assert(NJ <= 3, "phi region must fit three nodes per thread");
 };
 
+// One work item (z-chunk of one tile) of the two-component step.  Called by
+// every thread of the CTA (it synchronises the CTA).
 template <class L, class T, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, 2)
-    k_cg_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, CGPar<T> prm, Sched2 sc) {
+__device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict__ out, const Layout& lay,
+                                        const CGPar<T>& prm, const Sched2& sc, int it) {
     using C = CGCfg<L, T, BX, BY>;
     constexpr int NT = C::NT, HX1 = C::HX1, HN1 = C::HN1, HX2 = C::HX2, HN2 = C::HN2, NS = C::NS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(BX * BY, 2)
     // phi nodes of this thread: j = t + q NT (q < NJ) inside the tile + 2 halo
     constexpr int NJ = C::NJ;
 
-    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
+    {
         const int chunk = it / sc.ntiles, tile = it - chunk * sc.ntiles;
         const int x0 = (tile % sc.ncx) * BX, y0 = (tile / sc.ncx) * BY;
         const int za = chunk * sc.zc, zb = min(nz, za + sc.zc);
@@ -413,32 +431,39 @@ __global__ void __launch_bounds__(BX * BY, 2)
 
         Acc2<T> X, Y, Z;
         X.zero(); Y.zero(); Z.zero();
+        // wrapped plane indices, advanced without division: zs = source plane s,
+        // z1 = s + 1, z2 = s + 2; ring slots of planes s - 1, s, s + 1
+        int zs = pmod2(za - 1, nz);
+        int z1 = zs + 1 == nz ? 0 : zs + 1;
+        int z2 = z1 + 1 == nz ? 0 : z1 + 1;
+        int sm = 0, s0i = 1, sp = 2;
+        const int ox = x0 + tx, oy = y0 + ty;
+        const bool ghost = store_ok && (ox < kGhostX || ox >= nx - kGhostX || oy < lay.yo || oy >= ny - lay.yo);
+        T* out1 = out + (store_ok ? lay.at(ox, oy, za) : 0);
         for (int s = za - 1; s <= zb; ++s) {
             // (a) phi of plane s+1 from registers; prefetch for the next plane
-            const int slot_p = (s + 1 - za + 2) % 3;
 #pragma unroll
             for (int q = 0; q < NJ; ++q)
-                if (t + q * NT < HN2) PH[slot_p * HN2 + t + q * NT] = phi_of(pr1[q], pd[q]);
+                if (t + q * NT < HN2) PH[sp * HN2 + t + q * NT] = phi_of(pr1[q], pd[q]);
             Node2<T> n1next = m1, n2next = m2;
             if (s + 1 <= zb) {
-                const size_t zq = (size_t)pmod2(s + 2, nz) * plane;
+                const size_t zq = (size_t)z2 * plane;
 #pragma unroll
                 for (int q = 0; q < NJ; ++q)
                     if (t + q * NT < HN2) {
                         pr1[q] = __ldg(in + zq + offj[q]);
                         pd[q] = __ldg(in + fs + zq + offj[q]);
                     }
-                const size_t zn = (size_t)pmod2(s + 1, nz) * plane;
+                const size_t zn = (size_t)z1 * plane;
                 n1next = load_node2(in, zn + off1, fs);
                 if (role2) n2next = load_node2(in, zn + off2, fs);
             }
             __syncthreads();
             // (b) collide the source nodes of plane s and publish
-            const T* Pm = PH + ((s - 1 - za + 2) % 3) * HN2;
-            const T* P0 = PH + ((s - za + 2) % 3) * HN2;
-            const T* Pp = PH + slot_p * HN2;
-            const int gzs = pmod2(s, nz);
-            const Src2<T> c1 = collide2<L, T, HX2, HN2>(m1, Pm, P0, Pp, b1, prm, in, lay, gx1, gy1, gzs);
+            const T* Pm = PH + sm * HN2;
+            const T* P0 = PH + s0i * HN2;
+            const T* Pp = PH + sp * HN2;
+            const Src2<T> c1 = collide2<L, T, HX2, HN2>(m1, Pm, P0, Pp, b1, prm, in, lay, gx1, gy1, zs);
             publish2<L, T, HN1>(Gg, Gh, n1, c1);
             // own column (c_x = c_y = 0)
             const T s0 = g_shared(c1.c);
@@ -448,7 +473,7 @@ __global__ void __launch_bounds__(BX * BY, 2)
             const T ez = c1.e * wz * c1.nz;
             const T h_p = c1.r1 * (wz + g_p) + ez, h_m = c1.r1 * (wz + g_m) - ez, h_0 = c1.r1 * (w0 + g_0);
             if (role2) {
-                const Src2<T> c2 = collide2<L, T, HX2, HN2>(m2, Pm, P0, Pp, b2, prm, in, lay, gx2, gy2, gzs);
+                const Src2<T> c2 = collide2<L, T, HX2, HN2>(m2, Pm, P0, Pp, b2, prm, in, lay, gx2, gy2, zs);
                 if (role2 == 1) publish2<L, T, HN1, 2, 1>(Gg, Gh, n2, c2);
                 else if (role2 == 2) publish2<L, T, HN1, 2, -1>(Gg, Gh, n2, c2);
                 else publish2<L, T, HN1>(Gg, Gh, n2, c2);
@@ -459,13 +484,54 @@ __global__ void __launch_bounds__(BX * BY, 2)
             add_plane2<L, T, -1, HN1, HX1>(Gg, Gh, n1, g_m, h_m, X);
             add_plane2<L, T, 0, HN1, HX1>(Gg, Gh, n1, g_0, h_0, Y);
             add_plane2<L, T, 1, HN1, HX1>(Gg, Gh, n1, g_p, h_p, Z);
-            if (s - 1 >= za && store_ok) store_node2(out, lay, x0 + tx, y0 + ty, s - 1, X.r1, X.a.finish());
+            if (s - 1 >= za && store_ok) {
+                const Mom<T> r = X.a.finish();
+                store_node2_at(out1, fs, X.r1, r);
+                if (ghost) store_node2(out, lay, ox, oy, s - 1, X.r1, r);
+                out1 += plane;
+            }
             X = Y;
             Y = Z;
             m1 = n1next;
             m2 = n2next;
+            zs = z1;
+            z1 = z2;
+            z2 = z2 + 1 == nz ? 0 : z2 + 1;
+            const int tmp = sm;
+            sm = s0i;
+            s0i = sp;
+            sp = tmp;
         }
         __syncthreads();  // the phi ring and exchange buffers are reused by the next item
+    }
+}
+
+template <class L, class T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY, 2)
+    k_cg_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, CGPar<T> prm, Sched2 sc) {
+    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) cg_item<L, T, BX, BY>(in, out, lay, prm, sc, it);
+}
+
+// Batched ensemble: the items of every box, box after box, in one persistent
+// launch; a CTA finds the box of each item by binary search on item_begin.
+template <class L, class T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY, 2)
+    k_cg_batch(const BatchDom* __restrict__ doms, int ndom, int total, CGPar<T> prm) {
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = ndom - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (doms[mid].item_begin <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchDom d = doms[lo];
+        Sched2 sc;
+        sc.ncx = d.ncx;
+        sc.ntiles = d.ntiles;
+        sc.zc = d.zc;
+        sc.nitems = d.nitems;
+        cg_item<L, T, BX, BY>(static_cast<const T*>(d.in), static_cast<T*>(d.out), d.lay, prm, sc,
+                              it - d.item_begin);
     }
 }
 
@@ -522,6 +588,43 @@ cudaError_t cg_run_v(const llb_ctx& c, const void* in, void* out) {
     return cudaGetLastError();
 }
 
+template <class L, class T, int kBX2, int kBY2>
+int cg_batch_ctas_v(const llb_ctx& c) {
+    using C = CGCfg<L, T, kBX2, kBY2>;
+    auto kern = k_cg_batch<L, T, kBX2, kBY2>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::smem_bytes) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return per_sm * c.num_sms;
+}
+
+template <class L, class T, int kBX2, int kBY2>
+void cg_batch_plan_v(int nx, int ny, int nz, int grid, BatchDom* d) {
+    const Sched2 sc = plan2(nx, ny, nz, kBX2, kBY2, grid);
+    d->ncx = sc.ncx;
+    d->ntiles = sc.ntiles;
+    d->zc = sc.zc;
+    d->nitems = sc.nitems;
+}
+
+template <class L, class T, int kBX2, int kBY2>
+cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid) {
+    using C = CGCfg<L, T, kBX2, kBY2>;
+    CGPar<T> p;
+    p.omega = (T)c.omega;
+    p.beta = (T)c.params.beta;
+    p.A_s = (T)c.params.A_s;
+    p.A_h = (T)c.params.A_h;
+    p.g_min = (T)c.params.g_min;
+    p.g_nci = (T)kGNci;
+    p.h_c = c.params.h_c;
+    k_cg_batch<L, T, kBX2, kBY2><<<grid, C::NT, C::smem_bytes, c.stream>>>(doms, ndom, total, p);
+    return cudaGetLastError();
+}
+
 // Tile shapes: variant 0 = 64 x 4 (default), 1 = 32 x 8.
 template <class L, class T>
 int cg_ctas_t(const llb_ctx& c) {
@@ -537,6 +640,24 @@ cudaError_t cg_run_t(const llb_ctx& c, const void* in, void* out) {
 int cg_tiled_ctas(const llb_ctx& c) {
     if (c.Q == 19) return c.storage == LLB_F64 ? cg_ctas_t<D3Q19, double>(c) : cg_ctas_t<D3Q19, float>(c);
     return c.storage == LLB_F64 ? cg_ctas_t<D3Q27, double>(c) : cg_ctas_t<D3Q27, float>(c);
+}
+
+#define LLB_CG_BATCH(fn, ...)                                                                          \
+    if (c.Q == 19) {                                                                                   \
+        if (c.storage == LLB_F64)                                                                      \
+            return c.variant == 1 ? fn<D3Q19, double, 32, 8>(__VA_ARGS__) : fn<D3Q19, double, 64, 4>(__VA_ARGS__); \
+        return c.variant == 1 ? fn<D3Q19, float, 32, 8>(__VA_ARGS__) : fn<D3Q19, float, 64, 4>(__VA_ARGS__);       \
+    }                                                                                                  \
+    if (c.storage == LLB_F64)                                                                          \
+        return c.variant == 1 ? fn<D3Q27, double, 32, 8>(__VA_ARGS__) : fn<D3Q27, double, 64, 4>(__VA_ARGS__);     \
+    return c.variant == 1 ? fn<D3Q27, float, 32, 8>(__VA_ARGS__) : fn<D3Q27, float, 64, 4>(__VA_ARGS__);
+
+int cg_batch_ctas(const llb_ctx& c) { LLB_CG_BATCH(cg_batch_ctas_v, c) }
+void cg_batch_plan(const llb_ctx& c, int grid, BatchDom* d) {
+    LLB_CG_BATCH(cg_batch_plan_v, c.nx, c.ny, c.nz, grid, d)
+}
+cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid) {
+    LLB_CG_BATCH(cg_batch_run_v, c, doms, ndom, total, grid)
 }
 
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out) {

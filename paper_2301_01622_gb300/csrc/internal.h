@@ -51,6 +51,7 @@ struct llb_ctx {
     // captured step sequences (llb_step_graph): one per starting flip-flop copy
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     int graph_steps[2] = {0, 0};
+    bool in_batch = false;   // owned by an llb_batch: stepped and destroyed by it
 };
 
 namespace llb {
@@ -71,6 +72,20 @@ bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out);
 // Two-component colour-gradient moment-only step (cg_step.cu)
 int cg_tiled_ctas(const llb_ctx& c);
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out);
+
+// One box of a batched ensemble: its state copies for this step and its items.
+struct BatchDom {
+    const void* in;
+    void* out;
+    Layout lay;
+    int ncx, ntiles, zc, nitems;  // chunk-major schedule of the box
+    int item_begin;               // first global item of the box
+};
+// Persistent grid size of the batch kernel (ctx gives lattice, storage, variant).
+int cg_batch_ctas(const llb_ctx& c);
+// Fill the schedule fields of d for box c (c.nx.. give the box size) and `grid` CTAs.
+void cg_batch_plan(const llb_ctx& c, int grid, BatchDom* d);
+cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid);
 
 // Population-storing baselines (population_step.cu)
 cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);

@@ -373,14 +373,21 @@ __global__ void __launch_bounds__(BX * BY, MINB)
     for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
         int x0, y0, za, zb;  // outputs za .. zb-1 of the tile at (x0, y0)
         sc.item(it, BX, BY, nz, x0, y0, za, zb);
-        const size_t off1 = lay.at(pmod(x0 + tx, nx), pmod(y0 + ty, ny), 0);
-        const size_t off2 = lay.at(pmod(x0 - 1 + hx2, nx), pmod(y0 - 1 + hy2, ny), 0);
-        const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
+        const S* const in1 = in + lay.at(pmod(x0 + tx, nx), pmod(y0 + ty, ny), 0);
+        const S* const in2 = in + lay.at(pmod(x0 - 1 + hx2, nx), pmod(y0 - 1 + hy2, ny), 0);
+        const int ox = x0 + tx, oy = y0 + ty;
+        const bool store_ok = (ox < nx) && (oy < ny);
+        // periodic ghost copies are needed only near the x and y faces of the box
+        const bool ghost = store_ok && lay.ghosts &&
+                           (ox < kGhostX || ox >= nx - kGhostX || oy < lay.yo || oy >= ny - lay.yo);
+        S* out1 = out + (store_ok ? lay.at(ox, oy, za) : 0);   // output plane za, advanced per plane
 
-        int zs = pmod(za - 1, nz);
-        Mom<T> m1 = load_mom<T>(in, zs * plane + off1, lay.fs);
+        // source plane of the next load, wrapped incrementally (no division per plane)
+        int zn = pmod(za - 1, nz);
+        size_t zn_off = (size_t)zn * plane;
+        Mom<T> m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
         Mom<T> m2 = m1;
-        if (has2) m2 = load_mom<T>(in, zs * plane + off2, lay.fs);
+        if (has2) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
@@ -388,11 +395,15 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) {
             T* const G = Gbase + buf * (NS * HN);
             Mom<T> p1 = m1, p2 = m2;
-            const bool more = s + 1 <= zb;
-            if (more) {
-                const size_t zo = (size_t)pmod(s + 1, nz) * plane;
-                p1 = load_mom<T>(in, zo + off1, lay.fs);
-                if (has2) p2 = load_mom<T>(in, zo + off2, lay.fs);
+            if (s + 1 <= zb) {
+                if (++zn == nz) {
+                    zn = 0;
+                    zn_off = 0;
+                } else {
+                    zn_off += plane;
+                }
+                p1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
+                if (has2) p2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
             }
             const Mom<T> c1 = collide(m1, omega);
             publish<L, T, HN>(G, n1, c1);
@@ -401,7 +412,12 @@ __global__ void __launch_bounds__(BX * BY, MINB)
             if (has2) publish_halo<L, T, HN>(G, n2, role2, collide(m2, omega));
             __syncthreads();
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
-            if (s - 1 >= za && store_ok) store_node(out, lay, x0 + tx, y0 + ty, s - 1, X.finish());
+            if (s - 1 >= za && store_ok) {
+                const Mom<T> r = X.finish();
+                store_mom(out1, 0, lay.fs, r);
+                if (ghost) store_node(out, lay, ox, oy, s - 1, r);
+                out1 += plane;
+            }
             buf ^= 1;
             m1 = p1;
             m2 = p2;

@@ -79,6 +79,14 @@ _SIGS = {
                                           C.POINTER(llb_diag)]),
     "llb_steps_done": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "llb_state_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "llb_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_double,
+                                   C.POINTER(llb_params)]),
+    "llb_batch_destroy": (None, [C.c_void_p]),
+    "llb_batch_domain": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "llb_batch_nodes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "llb_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "llb_batch_step_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "llb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "llb_status_string": (C.c_char_p, [C.c_int]),
     "llb_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -262,3 +270,43 @@ def llb_state_device(ctx):
 
 def llb_last_error(ctx) -> str:
     return lib().llb_last_error(ctx).decode()
+
+
+def llb_batch_create(dims, lattice, tau, params: llb_params):
+    """dims: sequence of (nx, ny, nz); returns the batch handle."""
+    flat = (C.c_int * (3 * len(dims)))(*[int(v) for d in dims for v in d])
+    b = C.c_void_p()
+    _check(lib().llb_batch_create(C.byref(b), len(dims), flat, lattice, float(tau), C.byref(params)),
+           "llb_batch_create")
+    return b
+
+
+def llb_batch_destroy(b):
+    if b:
+        lib().llb_batch_destroy(b)
+
+
+def llb_batch_domain(b, d):
+    ctx = C.c_void_p()
+    _check(lib().llb_batch_domain(b, int(d), C.byref(ctx)), "llb_batch_domain")
+    return ctx
+
+
+def llb_batch_nodes(b) -> int:
+    v = C.c_longlong()
+    _check(lib().llb_batch_nodes(b, C.byref(v)), "llb_batch_nodes")
+    return int(v.value)
+
+
+def llb_batch_step(b, nsteps: int = 1):
+    _check(lib().llb_batch_step(b, int(nsteps)), "llb_batch_step")
+
+
+def llb_batch_step_graph(b, nsteps: int = 1):
+    _check(lib().llb_batch_step_graph(b, int(nsteps)), "llb_batch_step_graph")
+
+
+def llb_batch_autotune(b, trials: int = 3) -> int:
+    v = C.c_int()
+    _check(lib().llb_batch_autotune(b, int(trials), C.byref(v)), "llb_batch_autotune")
+    return v.value

@@ -288,3 +288,45 @@ def test_device_buffers_and_stream_from_torch():
     finally:
         llb.llb_destroy(ctx)
     assert_groups(got, lb.run_moment_only(m0, D3Q19, tau, 4), 1e-12, what="device buffers")
+
+
+@pytest.mark.parametrize("nsteps", [1, 4, 5])
+def test_step_graph_matches_step(nsteps):
+    """Steps replayed from a captured CUDA graph give bit-identical results,
+    also across repeated replays and both flip-flop parities."""
+    n = 48
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=3)
+    out = []
+    for use_graph in (False, True):
+        ctx = llb.llb_create(n, n, n, 19, 0.7, llb.llb_params_default())
+        try:
+            llb.llb_init_equilibrium(ctx, rho, u)
+            for _ in range(3):
+                (llb.llb_step_graph if use_graph else llb.llb_step)(ctx, nsteps)
+            assert llb.llb_steps_done(ctx) == 3 * nsteps
+            out.append(llb.llb_get_moments(ctx, np.empty((10, n, n, n))))
+        finally:
+            llb.llb_destroy(ctx)
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_autotune_keeps_state(q):
+    """The autotuner times kernels without advancing the state, then the chosen
+    kernel still matches the oracle."""
+    n = 72
+    rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=9)
+    ctx = llb.llb_create(n, n, n, q, 0.7, llb.llb_params_default())
+    try:
+        llb.llb_init_equilibrium(ctx, rho, u)
+        before = llb.llb_get_moments(ctx, np.empty((10, n, n, n)))
+        kernel, variant = llb.llb_autotune(ctx, 3)
+        after = llb.llb_get_moments(ctx, np.empty((10, n, n, n)))
+        assert np.array_equal(before, after) and llb.llb_steps_done(ctx) == 0
+        assert kernel in (llb.LLB_KERNEL_TILED, llb.LLB_KERNEL_TMA, llb.LLB_KERNEL_DIRECT)
+        llb.llb_step(ctx, 5)
+        got = llb.llb_get_moments(ctx, np.empty((10, n, n, n)))
+    finally:
+        llb.llb_destroy(ctx)
+    ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 5)
+    assert_groups(got, ref, 1e-5, what=f"autotuned kernel {kernel} variant {variant}")
