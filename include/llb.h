@@ -238,6 +238,21 @@ LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
  * the context runs (for profiling and zero-copy views). */
 LLB_API int llb_state_device(const llb_ctx* ctx, void** dev_ptr, int* dtype, int* kernel);
 
+/* Adjoint of nsteps one-component moment-only steps (FP32 or FP64 state):
+ * the gradient of a scalar loss L of the canonical moments after nsteps with
+ * respect to the canonical moments at the start and to tau.  The context
+ * must hold the starting state; it is restored before the call returns.
+ * dev_gfinal: dL/dm(t + nsteps), 10 canonical fields in device memory of
+ * element type dtype; dev_ginit: receives dL/dm(t) (same layout and dtype);
+ * *dtau receives dL/dtau (may be NULL).  The forward steps are run once with
+ * a checkpoint of the moments every `every` steps (0 = round(sqrt(nsteps)))
+ * and each segment is recomputed from its checkpoint during the backward
+ * sweep: ~nsteps/every + every state copies of device memory, allocated
+ * during the call.  Not in the paper (the paper has no gradients).
+ * Synchronises.  LLB_EINVAL for two components, 16-bit states, batch boxes. */
+LLB_API int llb_adjoint(llb_ctx* ctx, int nsteps, int every, const void* dev_gfinal, void* dev_ginit, int dtype,
+                        double* dtau);
+
 /* ---- batched ensembles ----------------------------------------------
  * Independent two-component boxes of (possibly) different sizes advanced
  * together: each step is ONE persistent launch whose CTAs walk the work

@@ -1,0 +1,302 @@
+// Hand-written adjoint of the one-component moment-only step.
+//
+// One step is m_new = S(C(m)) with
+//   C (pointwise collision): (d, j, A) -> (d, j, A' = (1 - omega) A + omega j j / rho), rho = 1 + d
+//   S (linear pull stencil): m_new(x) = sum_i e_i g_i(x - c_i),
+//       g_i = r_i . m' = w_i [d + 3 c_i.j + 4.5 c_i c_i : A' - 1.5 tr A'],
+//       e_i = (1, c_i, c_i c_i - cs^2 I) (the moments one unit of g_i carries).
+// Its adjoint maps a cotangent lam_new of m_new to the cotangent of m:
+//   lam'(y) = S^T lam_new (y) = sum_i r_i s_i,  s_i = e_i . lam_new(y + c_i)
+//   lam(y)  = J_C(m(y))^T lam'(y)
+// and accumulates dL/domega = sum_y lam'_A(y) : (j j / rho - A)(y).
+// The state A is stored as six entries; a cotangent of an off-diagonal entry
+// is the derivative with respect to that stored entry.
+//
+// llb_adjoint runs the forward steps once, keeping the state every K steps
+// (moments only), then walks the segments backwards: each segment is
+// recomputed from its checkpoint with its K states kept, and the adjoint
+// steps run through it in reverse (memory: ~N/K + K state copies).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "lattice.cuh"
+#include "layout.cuh"
+
+namespace llb {
+namespace {
+
+constexpr int kAdjThreads = 128;
+
+template <class T>
+__device__ __forceinline__ void load10(const T* __restrict__ p, size_t i, size_t fs, T* v) {
+#pragma unroll
+    for (int f = 0; f < 10; ++f) v[f] = p[f * fs + i];
+}
+
+// Adjoint of one step at source node y (one thread per node).  lam_new, m and
+// lam share the context's Layout; neighbours are addressed with the periodic
+// wrap (no ghost copies are needed in the cotangent arrays).
+template <class L, class T>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const T* __restrict__ lam_new, const T* __restrict__ m,
+                                                              T* __restrict__ lam, Layout lay, T omega,
+                                                              double* __restrict__ domega_rows) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    double part = 0.0;
+    if (x < lay.nx) {
+        // lam' = sum_i r_i (e_i . lam_new(y + c_i))
+        T ld = T(0), lj[3] = {T(0), T(0), T(0)}, la[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+            for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+                for (int cx = -1; cx <= 1; ++cx) {
+                    if (!L::has(cx, cy, cz)) continue;
+                    const size_t q = lay.at(wrap_idx(x + cx, lay.nx), wrap_idx(y + cy, lay.ny), wrap_idx(z + cz, lay.nz));
+                    T v[10];
+                    load10(lam_new, q, lay.fs, v);
+                    const T cxx = T(cx * cx) - T(kCs2), cyy = T(cy * cy) - T(kCs2), czz = T(cz * cz) - T(kCs2);
+                    // e_i . lam_new: the stored A entries carry (c_a c_b - cs^2 delta_ab)
+                    const T si = v[0] + T(cx) * v[1] + T(cy) * v[2] + T(cz) * v[3] + cxx * v[4] + cyy * v[5] +
+                                 czz * v[6] + T(cx * cy) * v[7] + T(cx * cz) * v[8] + T(cy * cz) * v[9];
+                    const T ws = T(L::w(cx, cy, cz)) * si;
+                    // r_i: dg/dd = w, dg/dj = 3 w c, dg/dA_aa = w (4.5 c_a^2 - 1.5), dg/dA_ab = 9 w c_a c_b
+                    ld += ws;
+                    lj[0] += T(3 * cx) * ws;
+                    lj[1] += T(3 * cy) * ws;
+                    lj[2] += T(3 * cz) * ws;
+                    la[0] += (T(4.5 * cx * cx) - T(1.5)) * ws;
+                    la[1] += (T(4.5 * cy * cy) - T(1.5)) * ws;
+                    la[2] += (T(4.5 * cz * cz) - T(1.5)) * ws;
+                    la[3] += T(9 * cx * cy) * ws;
+                    la[4] += T(9 * cx * cz) * ws;
+                    la[5] += T(9 * cy * cz) * ws;
+                }
+        // J_C^T at y
+        const size_t i0 = lay.at(x, y, z);
+        T s[10];
+        load10(m, i0, lay.fs, s);
+        const T rinv = T(1) / (T(1) + s[0]);
+        const T jx = s[1], jy = s[2], jz = s[3];
+        const T om = omega;
+        // A'_aa = (1-w) A_aa + w j_a^2 / rho ; A'_ab = (1-w) A_ab + w j_a j_b / rho
+        const T jj[6] = {jx * jx, jy * jy, jz * jz, jx * jy, jx * jz, jy * jz};
+        T dsum = T(0);
+        for (int k = 0; k < 6; ++k) dsum += la[k] * jj[k];
+        T out[10];
+        out[0] = ld - om * rinv * rinv * dsum;
+        out[1] = lj[0] + om * rinv * (T(2) * jx * la[0] + jy * la[3] + jz * la[4]);
+        out[2] = lj[1] + om * rinv * (T(2) * jy * la[1] + jx * la[3] + jz * la[5]);
+        out[3] = lj[2] + om * rinv * (T(2) * jz * la[2] + jx * la[4] + jy * la[5]);
+        for (int k = 0; k < 6; ++k) out[4 + k] = (T(1) - om) * la[k];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) lam[f * lay.fs + i0] = out[f];
+        // dL/domega: lam'_A : (j j / rho - A)
+        for (int k = 0; k < 6; ++k) part += (double)la[k] * ((double)jj[k] * (double)rinv - (double)s[4 + k]);
+    }
+    // block sum of the omega derivative (fixed order: warp shuffles then lanes of warp 0)
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    __shared__ double wsum[kAdjThreads / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sacc = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) sacc += wsum[w];
+        const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        domega_rows[b] = sacc;
+    }
+}
+
+// acc += sum of rows (one block, fixed order).
+__global__ void k_sum_rows(const double* __restrict__ rows, size_t n, double* __restrict__ acc) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += 256) s += rows[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += sh[0];
+}
+
+// Cotangents: canonical (rho, j, P) <-> shifted (d, j, A).  The forward maps are
+// d = rho - 1, A_aa = P_aa - cs^2 rho, A_ab = P_ab and back rho = 1 + d,
+// P_aa = A_aa + cs^2 (1 + d); the cotangent maps are their transposes.
+template <class T>
+__global__ void k_cot_canon_to_shifted(const void* __restrict__ g, int dt, T* __restrict__ lam, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        double v[10];
+        for (int f = 0; f < 10; ++f)
+            v[f] = dt == LLB_F64 ? static_cast<const double*>(g)[f * N + i] : (double)static_cast<const float*>(g)[f * N + i];
+        const int x = (int)(i % L.nx);
+        const size_t r = i / L.nx;
+        const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
+        lam[j] = (T)(v[0] + kCs2 * (v[4] + v[5] + v[6]));
+        for (int f = 1; f < 10; ++f) lam[f * L.fs + j] = (T)v[f];
+    }
+}
+
+template <class T>
+__global__ void k_cot_shifted_to_canon(const T* __restrict__ lam, void* __restrict__ g, int dt, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % L.nx);
+        const size_t r = i / L.nx;
+        const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
+        double v[10];
+        for (int f = 0; f < 10; ++f) v[f] = (double)lam[f * L.fs + j];
+        v[0] -= kCs2 * (v[4] + v[5] + v[6]);
+        for (int f = 0; f < 10; ++f) {
+            if (dt == LLB_F64) static_cast<double*>(g)[f * N + i] = v[f];
+            else static_cast<float*>(g)[f * N + i] = (float)v[f];
+        }
+    }
+}
+
+dim3 adj_grid(const llb_ctx& c) { return dim3((c.nx + kAdjThreads - 1) / kAdjThreads, c.ny, c.nz); }
+
+template <class L, class T>
+cudaError_t adj_step_t(const llb_ctx& c, const void* lam_new, const void* m, void* lam, double* rows) {
+    k_adjoint_step<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(static_cast<const T*>(lam_new),
+                                                                     static_cast<const T*>(m), static_cast<T*>(lam),
+                                                                     c.lay, (T)c.omega, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_step(const llb_ctx& c, const void* lam_new, const void* m, void* lam, double* rows) {
+    if (c.Q == 19)
+        return c.storage == LLB_F64 ? adj_step_t<D3Q19, double>(c, lam_new, m, lam, rows)
+                                    : adj_step_t<D3Q19, float>(c, lam_new, m, lam, rows);
+    return c.storage == LLB_F64 ? adj_step_t<D3Q27, double>(c, lam_new, m, lam, rows)
+                                : adj_step_t<D3Q27, float>(c, lam_new, m, lam, rows);
+}
+
+int grid_n(const llb_ctx& c) {
+    const size_t want = (c.N + 255) / 256;
+    const size_t cap = (size_t)(c.num_sms > 0 ? c.num_sms : 148) * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+// Advance the context by one step (same kernels as llb_step), flipping cur.
+cudaError_t fwd_one(llb_ctx* c) {
+    const void* in = c->buf[c->cur];
+    void* out = c->buf[1 - c->cur];
+    const cudaError_t e = c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, c->cur, out)
+                          : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
+                                                          : launch_moment_direct(*c, in, out);
+    if (e == cudaSuccess) c->cur = 1 - c->cur;
+    return e;
+}
+
+}  // namespace
+}  // namespace llb
+
+extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gfinal, void* dev_ginit, int dtype,
+                           double* dtau) {
+    using namespace llb;
+    if (!c) return LLB_EINVAL;
+    if (c->sticky != LLB_OK) return LLB_ESTATE;
+    if (c->in_batch || c->scheme != LLB_SCHEME_MOMENT || c->ncomp != 1 ||
+        (c->storage != LLB_F32 && c->storage != LLB_F64) || nsteps < 0 || !dev_gfinal || !dev_ginit ||
+        (dtype != LLB_F64 && dtype != LLB_F32))
+        return LLB_EINVAL;
+    const int K = every > 0 ? every : (int)std::fmax(1.0, std::round(std::sqrt((double)nsteps)));
+    const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    const size_t sb = c->state_bytes;
+    const size_t nrows = (size_t)adj_grid(*c).x * c->ny * c->nz;
+    // scratch: nseg checkpoints, K segment states, two cotangents, omega rows, accumulator
+    std::vector<void*> ptrs;
+    auto grab = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void* p : ptrs) cudaFree(p);
+        cudaGetLastError();
+    };
+    char* ck = static_cast<char*>(grab(sb * (size_t)(nseg > 0 ? nseg : 1)));
+    char* seg = static_cast<char*>(grab(sb * (size_t)K));
+    void* lamA = grab(sb);
+    void* lamB = grab(sb);
+    double* rows = static_cast<double*>(grab(nrows * sizeof(double)));
+    double* acc = static_cast<double*>(grab(sizeof(double)));
+    if (!ck || !seg || !lamA || !lamB || !rows || !acc) {
+        release();
+        return LLB_ENOMEM;
+    }
+    const int cur0 = c->cur;
+    const long long t0 = c->t;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), c->stream);
+    // forward with checkpoints (checkpoint k = state at step k K)
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+        if (s % K == 0)
+            e = cudaMemcpyAsync(ck + (size_t)(s / K) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = fwd_one(c);
+    }
+    // cotangent of the final state
+    if (e == cudaSuccess) {
+        if (c->storage == LLB_F64)
+            k_cot_canon_to_shifted<double><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<double*>(lamA), c->lay);
+        else
+            k_cot_canon_to_shifted<float><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<float*>(lamA), c->lay);
+        e = cudaGetLastError();
+    }
+    void* lam_in = lamA;
+    void* lam_out = lamB;
+    for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
+        const int s0 = k * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
+        // recompute the states s0 .. s1-1 of this segment from its checkpoint
+        e = cudaMemcpyAsync(c->buf[c->cur], ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, c->stream);
+        for (int s = s0; s < s1 && e == cudaSuccess; ++s) {
+            e = cudaMemcpyAsync(seg + (size_t)(s - s0) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess && s + 1 < s1) e = fwd_one(c);
+        }
+        for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
+            e = adj_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, rows);
+            if (e == cudaSuccess) {
+                k_sum_rows<<<1, 256, 0, c->stream>>>(rows, nrows, acc);
+                e = cudaGetLastError();
+            }
+            void* tmp = lam_in;
+            lam_in = lam_out;
+            lam_out = tmp;
+        }
+    }
+    // cotangent of the initial state, in canonical form
+    if (e == cudaSuccess) {
+        if (c->storage == LLB_F64)
+            k_cot_shifted_to_canon<double><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const double*>(lam_in), dev_ginit, dtype, c->lay);
+        else
+            k_cot_shifted_to_canon<float><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const float*>(lam_in), dev_ginit, dtype, c->lay);
+        e = cudaGetLastError();
+    }
+    double domega = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&domega, acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    // restore the initial state
+    if (e == cudaSuccess && nseg > 0) e = cudaMemcpyAsync(c->buf[cur0], ck, sb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->cur = cur0;
+    c->t = t0;
+    release();
+    if (e != cudaSuccess) {
+        c->sticky = LLB_ECUDA;
+        c->msg = std::string("adjoint: ") + cudaGetErrorString(e);
+        return LLB_ECUDA;
+    }
+    // omega = 1 / tau
+    if (dtau) *dtau = -domega / (c->tau * c->tau);
+    return LLB_OK;
+}

@@ -87,6 +87,8 @@ _SIGS = {
     "llb_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "llb_batch_step_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "llb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "llb_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                              C.POINTER(C.c_double)]),
     "llb_status_string": (C.c_char_p, [C.c_int]),
     "llb_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -225,6 +227,18 @@ def llb_autotune(ctx, trials: int = 5):
     k, v = C.c_int(), C.c_int()
     _check(lib().llb_autotune(ctx, int(trials), C.byref(k), C.byref(v)), "llb_autotune", ctx)
     return k.value, v.value
+
+
+def llb_adjoint(ctx, nsteps, gfinal_dev, ginit_dev, every: int = 0) -> float:
+    """Gradient of a loss w.r.t. the initial canonical moments (written into
+    ginit_dev) and tau (returned), given dL/d(final moments) in gfinal_dev."""
+    dt = _dtype_code(gfinal_dev)
+    if _dtype_code(ginit_dev) != dt:
+        raise TypeError("gfinal and ginit must have the same dtype")
+    dtau = C.c_double()
+    _check(lib().llb_adjoint(ctx, int(nsteps), int(every), _ptr(gfinal_dev), _ptr(ginit_dev), dt, C.byref(dtau)),
+           "llb_adjoint", ctx)
+    return float(dtau.value)
 
 
 def llb_get_moments(ctx, host_out):
