@@ -22,9 +22,12 @@ def _m0(n, seed, dtype=torch.float64):
 
 
 def _loss(mN, w):
-    # a non-linear field-mismatch loss: 0.5 |u - w|^2 with u = j / rho
+    # a non-linear field-mismatch loss: 0.5 |u - w|^2 with u = j / rho, plus the
+    # squared deviatoric flux (kept O(u^2) so that central differences are not
+    # swamped by the rounding of a large constant part)
     u = mN[1:4] / mN[0]
-    return 0.5 * ((u - w) ** 2).sum() + (mN[4:] * mN[4:]).sum()
+    dev = torch.cat([mN[4:7] - mN[0] / 3.0, mN[7:]])
+    return 0.5 * ((u - w) ** 2).sum() + 10.0 * (dev * dev).sum()
 
 
 @pytest.mark.parametrize("q", [19, 27])
