@@ -109,6 +109,13 @@ typedef struct llb_params {
      * the state, each at least llb_state_bytes() bytes and 256-byte aligned.
      * NULL = the library allocates (and frees) them.                       */
     void* buffers[2];
+    /* Bound on any wait inside a kernel (TMA stage arrival), in milliseconds
+     * of device clock; default 2000.  A wait that runs out makes the kernel
+     * record an error, let its own copies in flight land (with the default
+     * bound) and return; the next synchronising call reports LLB_ETIMEOUT.
+     * 0 makes every wait that is not already satisfied run out at once, which
+     * exercises that path without any fault (used by the tests). */
+    int wait_budget_ms;
 } llb_params;
 
 typedef struct llb_diag {

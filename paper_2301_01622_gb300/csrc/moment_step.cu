@@ -41,7 +41,7 @@
 namespace llb {
 namespace {
 
-constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) before a TMA wait gives up
+constexpr long long kDrainBudget = 4000000000LL;  // cycles (~2 s) to let copies in flight land after an abort
 
 // Ten shifted moments of node idx from a state of element type S (converted to T).
 template <class T, class S>
@@ -481,7 +481,7 @@ __device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int
 template <class L, class T, class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, Sched sc,
-                 int* __restrict__ err) {
+                 int* __restrict__ err, long long wait_budget) {
     constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS, NH = C::NH;
     constexpr int SF = C::SF, SW = C::SW;
     extern __shared__ unsigned char smem_raw[];
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
         auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) -> bool {
             const int k = q % NST;
-            const bool ok = mbar_wait_bounded(bar0 + 8 * k, (q / NST) & 1, kWaitBudget);
+            const bool ok = mbar_wait_bounded(bar0 + 8 * k, (q / NST) & 1, wait_budget);
             const T* const S = S0 + (size_t)k * (C::STAGE_STRIDE / sizeof(T));
             T* const G = Gbase + buf * (NS * HN);
             T g_m = T(0), g_0 = T(0), g_p = T(0);
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             if (t == 0) {
                 atomicExch(err, 1);
                 for (unsigned qq = q; qq < issued; ++qq)
-                    mbar_wait_bounded(bar0 + 8 * (qq % NST), (qq / NST) & 1, kWaitBudget);
+                    mbar_wait_bounded(bar0 + 8 * (qq % NST), (qq / NST) & 1, kDrainBudget);
             }
             return;
         }
@@ -680,8 +680,10 @@ template <class L, class T, class C>
 cudaError_t run_tma_c(const llb_ctx& c, int in_index, void* out) {
     const int grid = c.tma_ctas > 0 ? c.tma_ctas : 1;
     const Sched sc = plan(c.nx, c.ny, c.nz, C::BX, C::BY, grid);
+    // device clock ~2 GHz: cycles per millisecond
+    const long long budget = (long long)c.params.wait_budget_ms * 2000000LL;
     k_moment_tma<L, T, C><<<grid, C::NT, C::SMEM, c.stream>>>(c.tmap[in_index], static_cast<T*>(out), c.lay,
-                                                               (T)c.omega, sc, static_cast<int*>(c.err_dev));
+                                                               (T)c.omega, sc, static_cast<int*>(c.err_dev), budget);
     return cudaGetLastError();
 }
 
