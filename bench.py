@@ -448,7 +448,7 @@ def reference_arm(args, rank):
     val = nodes * args.steps / dt / 1e6
     sample = f"each step: one time step of a 256x256x{nzs} periodic slab of the workload (numpy FP64 oracle, 1 thread)"
     return {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_nodes_per_step": nodes},

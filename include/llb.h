@@ -113,9 +113,13 @@ typedef struct llb_params {
      * of device clock; default 2000.  A wait that runs out makes the kernel
      * record an error, let its own copies in flight land (with the default
      * bound) and return; the next synchronising call reports LLB_ETIMEOUT.
-     * 0 makes every wait that is not already satisfied run out at once, which
-     * exercises that path without any fault (used by the tests). */
+     * Range 1..600000. */
     int wait_budget_ms;
+    /* Fault injection for tests; 0 in normal use.  Bit 0: every TMA stage
+     * barrier is armed for one byte more than its copy delivers, so no stage
+     * wait can complete and every wait runs out after wait_budget_ms (the
+     * copies themselves land normally; nothing faults). */
+    int debug_flags;
 } llb_params;
 
 typedef struct llb_diag {

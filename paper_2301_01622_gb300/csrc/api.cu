@@ -77,7 +77,8 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
         *why = "unknown kernel"; return LLB_EINVAL;
     }
     if (p.variant < 0 || p.variant > 4) { *why = "variant must be in 0..4"; return LLB_EINVAL; }
-    if (p.wait_budget_ms < 0 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 0..600000"; return LLB_EINVAL; }
+    if (p.wait_budget_ms < 1 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 1..600000"; return LLB_EINVAL; }
+    if (p.debug_flags & ~1) { *why = "unknown debug flag"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
         if (p.scheme != LLB_SCHEME_MOMENT) { *why = "two components run only the moment-only scheme"; return LLB_EINVAL; }
         if (nx < 4 || ny < 4 || nz < 4) { *why = "two components need nx, ny, nz >= 4"; return LLB_EINVAL; }

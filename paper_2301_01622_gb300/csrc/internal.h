@@ -40,7 +40,6 @@ struct llb_ctx {
     size_t staging_bytes = 0;
     void* diag_scratch = nullptr;  // per-block partial sums of the diagnostics
     size_t diag_scratch_bytes = 0;
-    void* diag_moments = nullptr;  // moments of a population state, for diagnostics
     void* flag_dev = nullptr;      // device int for init-time checks
     long long t = 0;
     int sticky = LLB_OK;

@@ -41,7 +41,9 @@
 namespace llb {
 namespace {
 
-constexpr long long kDrainBudget = 4000000000LL;  // cycles (~2 s) to let copies in flight land after an abort
+// cycles (~50 ms) to let this CTA's copies in flight land after an abort: a
+// 16 KB box arrives within microseconds even under heavy load
+constexpr long long kDrainBudget = 100000000LL;
 
 // Ten shifted moments of node idx from a state of element type S (converted to T).
 template <class T, class S>
@@ -481,7 +483,7 @@ __device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int
 template <class L, class T, class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, Sched sc,
-                 int* __restrict__ err, long long wait_budget) {
+                 int* __restrict__ err, long long wait_budget, int extra_tx) {
     constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS, NH = C::NH;
     constexpr int SF = C::SF, SW = C::SW;
     extern __shared__ unsigned char smem_raw[];
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             for (int i = 0; i < NST && i < P; ++i) {
                 const unsigned qq = q0 + i;
                 const uint32_t bar = bar0 + 8 * (qq % NST);
-                mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
+                mbar_arrive_expect_tx(bar, C::STAGE_BYTES + extra_tx);
                 tma_load_4d(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(za - 1 + i, nz), 0,
                             bar);
             }
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 fence_proxy_async();
                 const unsigned qq = q + NST;
                 const uint32_t bar = bar0 + 8 * k;
-                mbar_arrive_expect_tx(bar, C::STAGE_BYTES);
+                mbar_arrive_expect_tx(bar, C::STAGE_BYTES + extra_tx);
                 tma_load_4d(stage0 + k * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(s + NST, nz), 0, bar);
                 issued = qq + 1;
             }
@@ -683,7 +685,8 @@ cudaError_t run_tma_c(const llb_ctx& c, int in_index, void* out) {
     // device clock ~2 GHz: cycles per millisecond
     const long long budget = (long long)c.params.wait_budget_ms * 2000000LL;
     k_moment_tma<L, T, C><<<grid, C::NT, C::SMEM, c.stream>>>(c.tmap[in_index], static_cast<T*>(out), c.lay,
-                                                               (T)c.omega, sc, static_cast<int*>(c.err_dev), budget);
+                                                               (T)c.omega, sc, static_cast<int*>(c.err_dev), budget,
+                                                               (c.params.debug_flags & 1) ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
     out[rank] = bench.reduce_max(1.5 + rank, w)
 
     class A:
-        steps, warmup, ref_budget = 1, 0, 1e-6
+        steps, warmup, ref_budget, gpus = 1, 0, 1e-6, 2
     out[world + rank] = 0.0 if bench.reference_arm(A(), r) is None else 1.0
     dist.destroy_process_group()
 

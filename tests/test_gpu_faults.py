@@ -1,7 +1,7 @@
-"""Failure handling without faulting the GPU: a device wait that runs out
-(injected by a zero wait budget) is reported as LLB_ETIMEOUT and leaves the
-CUDA context usable; an allocation larger than the device fails cleanly with
-LLB_ENOMEM."""
+"""Failure handling without faulting the GPU: a device wait that cannot
+complete (its barrier is armed for a byte that never arrives) runs out after
+its bound, is reported as LLB_ETIMEOUT and leaves the CUDA context usable; an
+allocation larger than the device fails cleanly with LLB_ENOMEM."""
 import numpy as np
 import pytest
 
@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 def test_wait_timeout_is_reported_and_context_stays_usable():
     n = 128
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05)
-    p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, wait_budget_ms=0)
+    p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, wait_budget_ms=20, debug_flags=1)
     ctx = llb.llb_create(n, n, n, 19, 0.8, p)
     try:
         llb.llb_init_equilibrium(ctx, rho, u)
@@ -40,6 +40,12 @@ def test_wait_timeout_is_reported_and_context_stays_usable():
         llb.llb_destroy(ctx)
     ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), D3Q19, 0.8, 5)
     assert np.abs(got - ref).max() < 1e-12
+
+
+def test_bad_wait_parameters_rejected():
+    for kw in ({"wait_budget_ms": 0}, {"debug_flags": 2}):
+        with pytest.raises(llb.LLBError):
+            llb.llb_footprint_query(8, 8, 8, 19, llb.llb_params_default(**kw))
 
 
 def test_allocation_failure_is_clean():
