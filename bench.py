@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the D3Q27 and population lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tma", "tiled", "direct"],
                     help="moment-only kernel (auto = the library's choice)")
-    ap.add_argument("--variant", type=int, default=0, help="TMA kernel variant (tuning)")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant (tuning; tiled 0..9, TMA 0..4)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="lattice of the main line")
     ap.add_argument("--cg-variant", type=int, default=0, help="two-component kernel variant (tuning)")
     ap.add_argument("--ref-budget", type=float, default=150.0,

@@ -95,9 +95,13 @@ typedef struct llb_params {
     int storage;      /* LLB_F32 (default), LLB_F64, LLB_F16S, LLB_BF16S     */
     int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
     int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
-    int variant;      /* tile/pipeline variant of the TMA and tiled kernels,
-                         0..4 (0 = default); tuning only, every variant
-                         computes the same result                            */
+    int variant;      /* tuning variant, 0 = default: tiled kernel 0..6
+                         (tile shape, CTAs per SM, split-phase plane
+                         barrier, IEEE or approximate FP32 1/rho), TMA
+                         kernel 0..4, two
+                         components 0..1; a variant the kernel does not have
+                         is LLB_EINVAL.  Every variant computes the same
+                         step (to FP32 rounding)                             */
     /* two-component colour-gradient / near-contact parameters (Sec. III A-B) */
     double beta;      /* recolouring strength, default 0.7                   */
     double A_s;       /* surface-tension (perturbation) strength, default 0.01 */

@@ -59,11 +59,22 @@ struct Mom {
     T d, jx, jy, jz, axx, ayy, azz, axy, axz, ayz;
 };
 
+// 1/rho.  FAST (FP32 only): the hardware approximate division (__fdividef,
+// within 2 ulp for rho of order one) instead of the IEEE-rounded quotient;
+// it enters only the non-linear term omega j j / rho.
+template <bool FAST, class T>
+__device__ __forceinline__ T inv_rho(T rho) {
+    if constexpr (FAST && sizeof(T) == 4)
+        return __fdividef(1.0f, rho);
+    else
+        return T(1) / rho;
+}
+
 // Collision: A' = (1 - omega) A + omega j j / rho; d and j are kept.
-template <class T>
+template <class T, bool FAST = false>
 __device__ __forceinline__ Mom<T> collide(const Mom<T>& m, T omega) {
     const T one_m = T(1) - omega;
-    const T rinv = T(1) / (T(1) + m.d);
+    const T rinv = inv_rho<FAST>(T(1) + m.d);
     const T ox = omega * m.jx * rinv, oy = omega * m.jy * rinv, oz = omega * m.jz * rinv;
     Mom<T> c;
     c.d = m.d;

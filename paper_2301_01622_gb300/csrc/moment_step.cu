@@ -232,55 +232,57 @@ __device__ __forceinline__ void own_column(const Mom<T>& c, T& g_m, T& g_0, T& g
 }
 
 // Add the populations that node n1 pulls from source plane s with c_z = CZ
-// into the accumulator of plane s + CZ.  Opposite directions in x (and y)
-// are combined first (sum and difference), so each moment gets one add per
-// pair instead of one per direction.
-template <class L, class T, int CZ>
+// into the accumulator of plane s + CZ (INIT: the accumulator starts here
+// and is assigned instead).  Opposite directions in x (and y) are combined
+// first (sum and difference), so each moment gets one add per pair instead
+// of one per direction; no partial sum starts from an explicit zero.
+template <class T, bool INIT>
+__device__ __forceinline__ void acc_to(T& a, T v) {
+    if constexpr (INIT) a = v; else a += v;
+}
+
+template <class L, class T, int CZ, bool INIT = false>
 __device__ __forceinline__ void add_plane(const T* __restrict__ g, T g_own, Acc<T>& A) {
-    T sum = g_own, jx = T(0), jy = T(0), sxx = T(0), syy = T(0), sxy = T(0);
-    if (L::has(1, 0, CZ)) {
-        const T a = g[kslot<L>(1, 0, CZ)], b = g[kslot<L>(-1, 0, CZ)];
-        const T s = a + b;
-        sum += s;
-        sxx += s;
-        jx += a - b;
-    }
-    if (L::has(0, 1, CZ)) {
-        const T a = g[kslot<L>(0, 1, CZ)], b = g[kslot<L>(0, -1, CZ)];
-        const T s = a + b;
-        sum += s;
-        syy += s;
-        jy += a - b;
-    }
-    if (L::has(1, 1, CZ)) {
+    static_assert(L::has(1, 0, CZ) && L::has(0, 1, CZ), "lattice without the axis-plane directions");
+    const T ax = g[kslot<L>(1, 0, CZ)], bx = g[kslot<L>(-1, 0, CZ)];
+    const T ay = g[kslot<L>(0, 1, CZ)], by = g[kslot<L>(0, -1, CZ)];
+    const T sx = ax + bx, sy = ay + by;
+    T jx = ax - bx, jy = ay - by;
+    T sxx = sx, syy = sy;
+    T sum = (g_own + sx) + sy;
+    if constexpr (L::has(1, 1, CZ)) {
         const T pp = g[kslot<L>(1, 1, CZ)], mm = g[kslot<L>(-1, -1, CZ)];
         const T pm = g[kslot<L>(1, -1, CZ)], mp = g[kslot<L>(-1, 1, CZ)];
         const T a = pp + mm, b = pm + mp, c = pp - mm, e = pm - mp;
-        const T s = a + b;
-        sum += s;
-        sxx += s;
-        syy += s;
-        sxy += a - b;
+        const T sd = a + b;
+        sum += sd;
+        sxx += sd;
+        syy += sd;
         jx += c + e;
         jy += c - e;
+        acc_to<T, INIT>(A.sxy, a - b);
+    } else if constexpr (INIT) {
+        A.sxy = T(0);
     }
-    A.d += sum;
-    A.jx += jx;
-    A.jy += jy;
-    A.sxx += sxx;
-    A.syy += syy;
-    A.sxy += sxy;
-    if (CZ != 0) {
-        A.szz += sum;
-        if (CZ > 0) {
-            A.jz += sum;
-            A.sxz += jx;
-            A.syz += jy;
+    acc_to<T, INIT>(A.d, sum);
+    acc_to<T, INIT>(A.jx, jx);
+    acc_to<T, INIT>(A.jy, jy);
+    acc_to<T, INIT>(A.sxx, sxx);
+    acc_to<T, INIT>(A.syy, syy);
+    if constexpr (CZ != 0) {
+        acc_to<T, INIT>(A.szz, sum);
+        if constexpr (CZ > 0) {
+            acc_to<T, INIT>(A.jz, sum);
+            acc_to<T, INIT>(A.sxz, jx);
+            acc_to<T, INIT>(A.syz, jy);
         } else {
+            static_assert(!INIT, "only the plane ahead starts here");
             A.jz -= sum;
             A.sxz -= jx;
             A.syz -= jy;
         }
+    } else {
+        static_assert(!INIT, "only the plane ahead starts here");
     }
 }
 
@@ -302,10 +304,9 @@ __device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T
                 const int k = kslot<L>(cx, cy, cz);
                 g[k] = G[k * HN + n1 - cy * HX - cx];
             }
-    Z.zero();
     add_plane<L, T, -1>(g, g_m, X);
     add_plane<L, T, 0>(g, g_0, Y);
-    add_plane<L, T, 1>(g, g_p, Z);
+    add_plane<L, T, 1, true>(g, g_p, Z);
 }
 
 // Halo node handled by thread t < NH and its role.  Threads [0, BX) take the
@@ -342,6 +343,14 @@ __device__ __forceinline__ void publish_halo(T* __restrict__ G, int n, int role,
 
 // ---------------------------------------------------------------------------
 // Tiled z-marching kernel, plain loads.
+// Options of the tiled kernel (bit flags):
+//   kSplit   -- split-phase plane barrier: each thread arrives on an mbarrier
+//               as soon as its populations are published, stores the plane
+//               finished one step earlier while the others catch up, and only
+//               then waits (bounded) before pulling; replaces __syncthreads.
+//   kFastRcp -- FP32 collision with the approximate division for 1/rho.
+constexpr int kSplit = 1, kFastRcp = 2;
+
 template <class L, class T, int BX, int BY>
 struct Tiled {
     static constexpr int NT = BX * BY;             // threads = output columns of a tile
@@ -349,18 +358,31 @@ struct Tiled {
     static constexpr int HN = HX * HY;
     static constexpr int NH = HN - NT;             // halo nodes, one per thread t < NH
     static constexpr int NS = n_xy_shifted<L>();   // directions crossing columns
-    static constexpr size_t smem_bytes = sizeof(T) * 2 * NS * HN;
+    static constexpr size_t g_bytes = sizeof(T) * 2 * NS * HN;
+    static constexpr size_t smem_bytes = g_bytes + 16;  // + two mbarriers (split-phase option)
     static_assert(NH <= NT, "halo must fit one node per thread");
+    static_assert(g_bytes % 8 == 0, "mbarriers need 8-byte alignment");
 };
 
-template <class L, class T, int BX, int BY, int MINB, class S>
+template <class L, class T, int BX, int BY, int MINB, int OPT, class S>
 __global__ void __launch_bounds__(BX * BY, MINB)
-    k_moment_tiled(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc) {
+    k_moment_tiled(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc, int* err,
+                   long long budget) {
     using K = Tiled<L, T, BX, BY>;
     constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
+    constexpr bool SPLIT = (OPT & kSplit) != 0, FAST = (OPT & kFastRcp) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const Gbase = reinterpret_cast<T*>(smem_raw);
+    const uint32_t bar0 = smem_u32(smem_raw + K::g_bytes);  // mbarrier of G buffer b at bar0 + 8 b
     const int nx = lay.nx, ny = lay.ny, nz = lay.nz;
+    if constexpr (SPLIT) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar0, K::NT);
+            mbar_init(bar0 + 8, K::NT);
+        }
+        __syncthreads();
+    }
+    uint32_t phase = 0;  // bit b: parity of the next phase of buffer b's mbarrier
 
     const int t = threadIdx.x;
     const int tx = t % BX, ty = t / BX;
@@ -388,53 +410,77 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         int zn = pmod(za - 1, nz);
         size_t zn_off = (size_t)zn * plane;
         Mom<T> m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
-        Mom<T> m2 = m1;
+        Mom<T> m2;
         if (has2) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
 
-        auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) {
+        auto put = [&](const Acc<T>& A, int z) {
+            const Mom<T> r = A.finish();
+            store_mom(out1, 0, lay.fs, r);
+            if (ghost) store_node(out, lay, ox, oy, z, r);
+            out1 += plane;
+        };
+
+        // One source plane s: X, Y, Z accumulate output planes s-1, s, s+1.
+        // Without kSplit, plane s-1 is finished and stored here; with kSplit
+        // it is stored in the next step (from Z, before Z restarts as s+2).
+        auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) -> bool {
             T* const G = Gbase + buf * (NS * HN);
-            Mom<T> p1 = m1, p2 = m2;
-            if (s + 1 <= zb) {
+            // the next source plane is loaded into m1 / m2 as soon as their
+            // collision is done (no second set of prefetch registers)
+            const bool more = s + 1 <= zb;
+            if (more) {
                 if (++zn == nz) {
                     zn = 0;
                     zn_off = 0;
                 } else {
                     zn_off += plane;
                 }
-                p1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
-                if (has2) p2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
             }
-            const Mom<T> c1 = collide(m1, omega);
+            const Mom<T> c1 = collide<T, FAST>(m1, omega);
+            if (more) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
             publish<L, T, HN>(G, n1, c1);
             T g_m, g_0, g_p;
             own_column<L, T>(c1, g_m, g_0, g_p);
-            if (has2) publish_halo<L, T, HN>(G, n2, role2, collide(m2, omega));
-            __syncthreads();
-            gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
-            if (s - 1 >= za && store_ok) {
-                const Mom<T> r = X.finish();
-                store_mom(out1, 0, lay.fs, r);
-                if (ghost) store_node(out, lay, ox, oy, s - 1, r);
-                out1 += plane;
+            if (has2) {
+                const Mom<T> c2 = collide<T, FAST>(m2, omega);
+                if (more) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
+                publish_halo<L, T, HN>(G, n2, role2, c2);
             }
+            if constexpr (SPLIT) {
+                const uint32_t bar = bar0 + 8 * buf;
+                mbar_arrive(bar);
+                if (s - 2 >= za && store_ok) put(Z, s - 2);
+                if (!mbar_wait_bounded(bar, (phase >> buf) & 1u, budget)) {
+                    atomicExch(err, 2);
+                    return false;
+                }
+                phase ^= 1u << buf;
+            } else {
+                __syncthreads();
+            }
+            gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
+            if (!SPLIT && s - 1 >= za && store_ok) put(X, s - 1);
             buf ^= 1;
-            m1 = p1;
-            m2 = p2;
+            return true;
+        };
+        // the accumulator of the last output plane (zb - 1) when the march ends
+        auto last = [&](const Acc<T>& X) {
+            if (SPLIT && store_ok && zb - 1 >= za) put(X, zb - 1);
         };
 
-        int s = za - 1;
+        int s = za - 1;  // za - 1 < zb: every item has at least one output plane
         for (;;) {
-            if (s > zb) break;
-            plane_step(s, a0, a1, a2);
+            if (!plane_step(s, a0, a1, a2)) return;
+            if (s == zb) { last(a0); break; }
             ++s;
-            if (s > zb) break;
-            plane_step(s, a1, a2, a0);
+            if (!plane_step(s, a1, a2, a0)) return;
+            if (s == zb) { last(a1); break; }
             ++s;
-            if (s > zb) break;
-            plane_step(s, a2, a0, a1);
+            if (!plane_step(s, a2, a0, a1)) return;
+            if (s == zb) { last(a2); break; }
             ++s;
         }
     }
@@ -616,22 +662,27 @@ cudaError_t run_direct(const llb_ctx& c, const void* in, void* out) {
 }
 
 // Plain-load tiled kernel variants (tile BX x BY, CTAs per SM the register
-// budget targets); variant 0 is the default.
-template <int BX_, int BY_, int MINB_>
+// budget targets, options); variant 0 is the default.
+template <int BX_, int BY_, int MINB_, int OPT_ = 0>
 struct TiledShape {
-    static constexpr int BX = BX_, BY = BY_, MINB = MINB_;
+    static constexpr int BX = BX_, BY = BY_, MINB = MINB_, OPT = OPT_;
 };
-template <class T, int V> struct TiledVariant { using type = TiledShape<64, 4, 2>; };
-template <> struct TiledVariant<float, 1> { using type = TiledShape<64, 8, 1>; };
-template <> struct TiledVariant<float, 2> { using type = TiledShape<96, 4, 1>; };
-template <> struct TiledVariant<float, 3> { using type = TiledShape<32, 8, 2>; };
-template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1>; };
+// FP32: the approximate 1/rho is the default (measured ~1.5 % faster at
+// 256^3, error far below FP32 storage rounding); variant 5 keeps the
+// IEEE-rounded division, variant 6 adds the split-phase plane barrier.
+template <class T, int V> struct TiledVariant { using type = TiledShape<64, 4, 2, kFastRcp>; };
+template <> struct TiledVariant<float, 1> { using type = TiledShape<64, 8, 1, kFastRcp>; };
+template <> struct TiledVariant<float, 2> { using type = TiledShape<96, 4, 1, kFastRcp>; };
+template <> struct TiledVariant<float, 3> { using type = TiledShape<32, 8, 2, kFastRcp>; };
+template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1, kFastRcp>; };
+template <> struct TiledVariant<float, 5> { using type = TiledShape<64, 4, 2>; };
+template <> struct TiledVariant<float, 6> { using type = TiledShape<64, 4, 2, kSplit | kFastRcp>; };
 template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
 
 template <class L, class T, class St, class S>
 int tiled_ctas_c(const llb_ctx& c) {
     using K = Tiled<L, T, S::BX, S::BY>;
-    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB, St>;
+    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
@@ -647,8 +698,11 @@ cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
     using K = Tiled<L, T, S::BX, S::BY>;
     const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
     const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, grid);
-    k_moment_tiled<L, T, S::BX, S::BY, S::MINB, St><<<grid, K::NT, K::smem_bytes, c.stream>>>(
-        static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc);
+    // device clock ~2 GHz: cycles per millisecond
+    const long long budget = (long long)c.params.wait_budget_ms * 2000000LL;
+    k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St><<<grid, K::NT, K::smem_bytes, c.stream>>>(
+        static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc, static_cast<int*>(c.err_dev),
+        budget);
     return cudaGetLastError();
 }
 
@@ -658,6 +712,8 @@ cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
         case 2: return fn<L, T, St, typename TiledVariant<T, 2>::type>(__VA_ARGS__);         \
         case 3: return fn<L, T, St, typename TiledVariant<T, 3>::type>(__VA_ARGS__);         \
         case 4: return fn<L, T, St, typename TiledVariant<T, 4>::type>(__VA_ARGS__);         \
+        case 5: return fn<L, T, St, typename TiledVariant<T, 5>::type>(__VA_ARGS__);         \
+        case 6: return fn<L, T, St, typename TiledVariant<T, 6>::type>(__VA_ARGS__);         \
         default: return fn<L, T, St, typename TiledVariant<T, 0>::type>(__VA_ARGS__);        \
     }
 
@@ -668,6 +724,7 @@ cudaError_t run_tiled(const llb_ctx& c, const void* in, void* out) { LLB_TILED_V
 
 template <class L, class T, class C>
 int tma_ctas_c(const llb_ctx& c) {
+    if (c.variant >= kTmaVariants) return 0;  // the TMA kernel has variants 0..4 only
     if (!c.lay.ghosts || c.lay.px < C::SW || c.lay.py < C::SR) return 0;
     auto kern = k_moment_tma<L, T, C>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return 0;

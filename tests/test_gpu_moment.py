@@ -96,13 +96,16 @@ def _oracle_ragged(q):
     return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("kernel", [llb.LLB_KERNEL_TMA, llb.LLB_KERNEL_TILED], ids=["tma", "tiled"])
+KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(7)]
+
+
+@pytest.mark.parametrize("kernel, variant", KERNEL_VARIANTS,
+                         ids=[f"{'tma' if k == llb.LLB_KERNEL_TMA else 'tiled'}-v{v}" for k, v in KERNEL_VARIANTS])
 @pytest.mark.parametrize("q", [19, 27])
 def test_kernel_variants_match_oracle(variant, kernel, q):
     """Every tuning variant of the z-marching kernels (tile shape, ring depth,
-    CTAs/SM) computes the same step: ragged multi-tile box, FP32, 1e-5 after
-    20 steps."""
+    CTAs/SM, split-phase plane barrier, approximate 1/rho) computes the same
+    step: ragged multi-tile box, FP32, 1e-5 after 20 steps."""
     shape = (133, 37, 29)
     rho, u = inputs.taylor_green_3d(*shape, u0=0.05, noise=1e-3, seed=7)
     try:
@@ -113,6 +116,15 @@ def test_kernel_variants_match_oracle(variant, kernel, q):
         pytest.skip("variant does not fit on this lattice")
     assert used == kernel
     assert_groups(got, _oracle_ragged(q), 1e-5, what=f"variant {variant}")
+
+
+def test_tma_kernel_has_five_variants():
+    """Variants 5..6 exist for the plain-load kernel only: asking the TMA
+    kernel for one is refused at creation."""
+    p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, variant=5)
+    with pytest.raises(llb.LLBError) as e:
+        llb.llb_create(64, 64, 64, 19, 0.8, p)
+    assert e.value.status == llb.LLB_EINVAL
 
 
 @pytest.mark.parametrize("q", [19, 27])

@@ -132,3 +132,34 @@ def test_colour_conservation_and_diagnostics(q):
     assert d1["n_in"] == int(inside.sum())
     assert abs(d1["rho1_avg"] - float(m[0][inside].mean())) < 1e-12
     assert abs(d1["mass"][0] - float(m[0].sum())) < 1e-10 * n
+
+
+@pytest.mark.parametrize("A_h, expect", [(0.0, 1), (0.2, 2)], ids=["no-nci-merges", "nci-stays-apart"])
+def test_near_contact_force_outcome(A_h, expect):
+    """Head-on pair (R = 14, 6 nodes apart, closing at 0.1) in 128 x 64 x 64,
+    D3Q27 FP32, tau = 1: without the near-contact force the droplets coalesce
+    into one; with a repulsion A_h = 0.2 they stay two droplets with the major
+    component between them.  This is the qualitative outcome of Sec. IV
+    (Fig. 1 with the repulsion of Sec. III B, Fig. 6 with A_h = 0); the paper's
+    A_h = 0.01 belongs to its own force normalisation, and under this library's
+    reading (F = A_h G on the near-contact band) 0.01 is too weak to stop this
+    approach, while 0.05 and above keep the pair apart.  The colour masses
+    are conserved either way."""
+    shape = (128, 64, 64)
+    r1, r2, u = _pair(shape, 14.0, 6.0, 0.05, 0.0)
+    p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F32, A_h=A_h, A_s=0.01, beta=0.7)
+    ctx = llb.llb_create(*shape, 27, 1.0, p)
+    try:
+        llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
+        d0 = llb.llb_diagnostics(ctx)
+        llb.llb_step(ctx, 1200)
+        d1 = llb.llb_diagnostics(ctx)
+        m = llb.llb_get_moments(ctx, np.empty((11,) + shape[::-1], dtype=np.float32))
+    finally:
+        llb.llb_destroy(ctx)
+    assert tc.count_droplets(m[0]) == expect
+    phi = (m[0] - m[1]) / (m[0] + m[1])
+    gap_min = float(phi[32, 32, 61:68].min())
+    assert (gap_min < -0.9) if expect == 2 else (gap_min > 0.9)
+    for k in range(2):
+        assert abs(d1["mass"][k] - d0["mass"][k]) < 1e-5 * d0["mass"][k]
