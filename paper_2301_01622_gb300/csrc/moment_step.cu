@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(BX * BY, MINB)
     k_moment_tiled(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc, int* err,
                    long long budget) {
     using K = Tiled<L, T, BX, BY>;
-    constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NH = K::NH;
+    constexpr int HX = K::HX, HN = K::HN, NS = K::NS;
     constexpr bool SPLIT = (OPT & kSplit) != 0, FAST = (OPT & kFastRcp) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const Gbase = reinterpret_cast<T*>(smem_raw);
@@ -530,7 +530,7 @@ template <class L, class T, class C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, Sched sc,
                  int* __restrict__ err, long long wait_budget, int extra_tx) {
-    constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS, NH = C::NH;
+    constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS;
     constexpr int SF = C::SF, SW = C::SW;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
