@@ -582,6 +582,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
+        const int ox = x0 + tx, oy = y0 + ty;
+        // periodic ghost copies are needed only near the x and y faces of the box
+        const bool ghost = store_ok && (ox < kGhostX || ox >= nx - kGhostX || oy < lay.yo || oy >= ny - lay.yo);
+        T* out1 = out + (store_ok ? lay.at(ox, oy, za) : 0);   // output plane za, advanced per plane
+        const size_t plane = (size_t)lay.px * lay.py;
 
         auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) -> bool {
             const int k = q % NST;
@@ -590,10 +595,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             T* const G = Gbase + buf * (NS * HN);
             T g_m = T(0), g_0 = T(0), g_p = T(0);
             if (ok) {
-                const Mom<T> c1 = collide(stage_mom<T, SF, SW>(S, tx + 1, ty + 1), omega);
+                const Mom<T> c1 = collide<T, true>(stage_mom<T, SF, SW>(S, tx + 1, ty + 1), omega);
                 publish<L, T, HN>(G, n1, c1);
                 own_column<L, T>(c1, g_m, g_0, g_p);
-                if (has2) publish_halo<L, T, HN>(G, n2, role2, collide(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
+                if (has2)
+                    publish_halo<L, T, HN>(G, n2, role2, collide<T, true>(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
             }
             if (__syncthreads_or(!ok)) return false;
             // every thread is done with stage k: refill it with plane s + NST
@@ -606,7 +612,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 issued = qq + 1;
             }
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
-            if (s - 1 >= za && store_ok) store_node(out, lay, x0 + tx, y0 + ty, s - 1, X.finish());
+            if (s - 1 >= za && store_ok) {
+                const Mom<T> r = X.finish();
+                store_mom(out1, 0, lay.fs, r);
+                if (ghost) store_node(out, lay, ox, oy, s - 1, r);
+                out1 += plane;
+            }
             buf ^= 1;
             ++q;
             return true;
@@ -645,10 +656,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // the default; the others exist for tuning sweeps (llb_params.variant).
 template <class L, class T, int V>
 struct TmaVariant;
-template <class L> struct TmaVariant<L, float, 0> { using type = TmaCfg<L, float, 64, 4, 4, 2>; };
+// Ring depths are chosen so that two CTAs of the 256-thread tiles fit in
+// the shared memory of one SM (2-3 x 17 KB stages + 51 KB exchange buffers);
+// the 2-deep ring measured fastest on 256^3.
+template <class L> struct TmaVariant<L, float, 0> { using type = TmaCfg<L, float, 64, 4, 2, 2>; };
 template <class L> struct TmaVariant<L, float, 1> { using type = TmaCfg<L, float, 64, 8, 3, 1>; };
-template <class L> struct TmaVariant<L, float, 2> { using type = TmaCfg<L, float, 96, 4, 3, 1>; };
-template <class L> struct TmaVariant<L, float, 3> { using type = TmaCfg<L, float, 32, 8, 4, 2>; };
+template <class L> struct TmaVariant<L, float, 2> { using type = TmaCfg<L, float, 64, 4, 3, 2>; };
+template <class L> struct TmaVariant<L, float, 3> { using type = TmaCfg<L, float, 32, 8, 3, 2>; };
 template <class L> struct TmaVariant<L, float, 4> { using type = TmaCfg<L, float, 128, 4, 3, 1>; };
 template <class L, int V> struct TmaVariant<L, double, V> { using type = TmaCfg<L, double, 32, 8, 2, 1>; };
 constexpr int kTmaVariants = 5;
@@ -677,6 +691,7 @@ template <> struct TiledVariant<float, 3> { using type = TiledShape<32, 8, 2, kF
 template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1, kFastRcp>; };
 template <> struct TiledVariant<float, 5> { using type = TiledShape<64, 4, 2>; };
 template <> struct TiledVariant<float, 6> { using type = TiledShape<64, 4, 2, kSplit | kFastRcp>; };
+template <> struct TiledVariant<float, 7> { using type = TiledShape<32, 4, 4, kFastRcp>; };
 template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
 
 template <class L, class T, class St, class S>
@@ -714,6 +729,7 @@ cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
         case 4: return fn<L, T, St, typename TiledVariant<T, 4>::type>(__VA_ARGS__);         \
         case 5: return fn<L, T, St, typename TiledVariant<T, 5>::type>(__VA_ARGS__);         \
         case 6: return fn<L, T, St, typename TiledVariant<T, 6>::type>(__VA_ARGS__);         \
+        case 7: return fn<L, T, St, typename TiledVariant<T, 7>::type>(__VA_ARGS__);         \
         default: return fn<L, T, St, typename TiledVariant<T, 0>::type>(__VA_ARGS__);        \
     }
 

@@ -96,7 +96,7 @@ def _oracle_ragged(q):
     return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
 
 
-KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(7)]
+KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(8)]
 
 
 @pytest.mark.parametrize("kernel, variant", KERNEL_VARIANTS,
@@ -119,7 +119,7 @@ def test_kernel_variants_match_oracle(variant, kernel, q):
 
 
 def test_tma_kernel_has_five_variants():
-    """Variants 5..6 exist for the plain-load kernel only: asking the TMA
+    """Variants 5..7 exist for the plain-load kernel only: asking the TMA
     kernel for one is refused at creation."""
     p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, variant=5)
     with pytest.raises(llb.LLBError) as e:
