@@ -33,6 +33,10 @@ repository's design notes, one per step:
    applied to these populations (Sec. III A, last sentence) where the normal
    is defined (|G| >= g_min); elsewhere Delta_i = 0 (with n = 0 the bracket
    would not sum to zero and would create mass).
+   With a smooth norm (eps > 0, a reading for gradients only):
+   |G|_eps = sqrt(|G|^2 + eps^2), n = G / |G|_eps at every node and
+       Delta_i = (A_s / 2) |G|_eps [w_i (c_i.n)^2 - w_i cs^2 |n|^2],
+   which sums to zero and whose second moment is A_s cs^4 |G|_eps n n.
 4. recolouring of the collided populations (Sec. III A):
        h1'_i = (rho1/rho) h'_i + beta (rho1 rho2 / rho) w_i (c_i.n) / |c_i|   (0 for c_i = 0),
        h2'_i = h'_i - h1'_i.
@@ -66,6 +70,7 @@ class CGParams:
     g_min: float = 1e-8   # |G| below which the normal is zero
     h_c: int = 3          # near-contact probe range (nodes)
     g_nci: float = 0.05   # |G| above which a node belongs to the interface band of the detector
+    eps: float = 0.0      # > 0: smooth norm |G|_eps = sqrt(|G|^2 + eps^2), normal G/|G|_eps everywhere
 
 
 def _check(m):
@@ -102,8 +107,13 @@ def gradient(phi: np.ndarray, lat: Lattice) -> np.ndarray:
     return G / CS2
 
 
-def unit_normal(G: np.ndarray, g_min: float):
-    """(|G|, n) with n = G/|G| where |G| >= g_min, n = 0 elsewhere."""
+def unit_normal(G: np.ndarray, g_min: float, eps: float = 0.0):
+    """(|G|, n, defined): n = G/|G| where |G| >= g_min, n = 0 elsewhere; with
+    eps > 0 the smooth norm |G|_eps = sqrt(|G|^2 + eps^2) and n = G/|G|_eps at
+    every node (|n| < 1, the step stays differentiable where G -> 0)."""
+    if eps > 0.0:
+        gn = np.sqrt(G[0] ** 2 + G[1] ** 2 + G[2] ** 2 + eps * eps)
+        return gn, G / gn, np.ones(gn.shape, dtype=bool)
     gn = np.sqrt(G[0] ** 2 + G[1] ** 2 + G[2] ** 2)
     iface = gn >= g_min
     n = np.zeros_like(G)
@@ -143,7 +153,7 @@ class CollisionFields:
         self.rho = self.fl.rho
         self.phi = (self.rho1 - self.rho2) / self.rho
         self.G = gradient(self.phi, lat)
-        self.gnorm, self.n, self.iface = unit_normal(self.G, prm.g_min)
+        self.gnorm, self.n, self.iface = unit_normal(self.G, prm.g_min, prm.eps)
         if prm.A_h != 0.0:
             self.near = near_contact(self.phi, self.n, self.gnorm >= prm.g_nci, prm.h_c)
         else:
@@ -170,8 +180,13 @@ def collided_direction(cf: CollisionFields, lat: Lattice, i: int):
     uFdot = u[0] * F[0] + u[1] * F[1] + u[2] * F[2]
     S = w * ((cF - uFdot) / CS2 + (c[0] * u[0] + c[1] * u[1] + c[2] * u[2]) * cF / (CS2 * CS2))
     cn = c[0] * cf.n[0] + c[1] * cf.n[1] + c[2] * cf.n[2]
-    # the perturbation acts only where the interface normal is defined
-    pert = np.where(cf.iface, 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2), 0.0)
+    # the perturbation acts only where the interface normal is defined; with the
+    # smooth norm (|n| < 1) its trace term carries |n|^2 so that it still sums to zero
+    if cf.prm.eps > 0.0:
+        nn = cf.n[0] ** 2 + cf.n[1] ** 2 + cf.n[2] ** 2
+        pert = 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2 * nn)
+    else:
+        pert = np.where(cf.iface, 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2), 0.0)
     hp = (1.0 - om) * h + om * heq + (1.0 - 0.5 * om) * S + pert          # Eq. (coll) + forcing + perturbation
     cnorm = np.sqrt((c * c).sum())
     recol = 0.0 if cnorm == 0 else cf.prm.beta * (cf.rho1 * cf.rho2 / rho) * w * cn / cnorm
