@@ -124,6 +124,13 @@ typedef struct llb_params {
      * wait can complete and every wait runs out after wait_budget_ms (the
      * copies themselves land normally; nothing faults). */
     int debug_flags;
+    /* Two components: 0 (default) takes the interface normal n = G/|G| only
+     * where |G| >= g_min (n = 0 elsewhere).  eps > 0 takes the smooth norm
+     * |G|_eps = sqrt(|G|^2 + eps^2) and n = G/|G|_eps at every node, with the
+     * perturbation's trace term scaled by |n|^2 so that it still conserves
+     * mass; the step is then differentiable (llb_adjoint of two components
+     * requires it).  Not in the paper: a reading for gradients. */
+    double grad_eps;
 } llb_params;
 
 typedef struct llb_diag {
@@ -253,18 +260,21 @@ LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
  * the context runs (for profiling and zero-copy views). */
 LLB_API int llb_state_device(const llb_ctx* ctx, void** dev_ptr, int* dtype, int* kernel);
 
-/* Adjoint of nsteps one-component moment-only steps (FP32 or FP64 state):
- * the gradient of a scalar loss L of the canonical moments after nsteps with
- * respect to the canonical moments at the start and to tau.  The context
- * must hold the starting state; it is restored before the call returns.
- * dev_gfinal: dL/dm(t + nsteps), 10 canonical fields in device memory of
- * element type dtype; dev_ginit: receives dL/dm(t) (same layout and dtype);
- * *dtau receives dL/dtau (may be NULL).  The forward steps are run once with
- * a checkpoint of the moments every `every` steps (0 = round(sqrt(nsteps)))
- * and each segment is recomputed from its checkpoint during the backward
- * sweep: ~nsteps/every + every state copies of device memory, allocated
- * during the call.  Not in the paper (the paper has no gradients).
- * Synchronises.  LLB_EINVAL for two components, 16-bit states, batch boxes. */
+/* Adjoint of nsteps moment-only steps (FP32 or FP64 state): the gradient of
+ * a scalar loss L of the canonical moments after nsteps with respect to the
+ * canonical moments at the start and to tau.  The context must hold the
+ * starting state; it is restored before the call returns.
+ * dev_gfinal: dL/dm(t + nsteps), 10 (one component) or 11 (two components)
+ * canonical fields in device memory of element type dtype; dev_ginit:
+ * receives dL/dm(t) (same layout and dtype); *dtau receives dL/dtau (may be
+ * NULL).  The forward steps are run once with a checkpoint of the moments
+ * every `every` steps (0 = round(sqrt(nsteps))) and each segment is
+ * recomputed from its checkpoint during the backward sweep: ~nsteps/every +
+ * every state copies of device memory, allocated during the call.  Two
+ * components need A_h = 0 (the near-contact switch is not differentiable)
+ * and grad_eps > 0 (the smooth interface normal).  Not in the paper (the
+ * paper has no gradients).  Synchronises.  LLB_EINVAL for 16-bit states,
+ * batch boxes, or two components without those two settings. */
 LLB_API int llb_adjoint(llb_ctx* ctx, int nsteps, int every, const void* dev_gfinal, void* dev_ginit, int dtype,
                         double* dtau);
 

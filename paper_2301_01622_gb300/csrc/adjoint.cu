@@ -12,6 +12,17 @@
 // The state A is stored as six entries; a cotangent of an off-diagonal entry
 // is the derivative with respect to that stored entry.
 //
+// Two components (A_h = 0, smooth normal |G|_eps): the state is (rho1, d, j,
+// A) and a source node y emits g'_i (as above, with A' gaining
+// ks n n, ks = A_s |G|_eps / 9, n = G / |G|_eps) and the colour population
+//   h1'_i = (rho1 / rho)(w_i + g'_i) + e w_i (c_i.n) / |c_i|,  e = beta rho1 (rho - rho1) / rho,
+// where G(y) = 3 sum_k w_k c_k phi(y + c_k), phi = 2 rho1 / rho - 1.  The
+// adjoint runs in two passes: per node y, the cotangents of y's own fields
+// and of G(y) (pull transposed, then the node's collision, perturbation and
+// recolouring transposed); then per node z, the transposed gradient stencil
+// lam_phi(z) = 3 sum_k w_k c_k . lam_G(z - c_k), added through phi(z) to
+// lam_rho1(z) and lam_d(z).
+//
 // llb_adjoint runs the forward steps once, keeping the state every K steps
 // (moments only), then walks the segments backwards: each segment is
 // recomputed from its checkpoint with its K states kept, and the adjoint
@@ -111,6 +122,184 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const T* __restric
     }
 }
 
+template <class T>
+struct CGAdjPar {
+    T omega, beta, A_s, eps2;
+};
+
+__host__ __device__ constexpr double inv_len_c(int cx, int cy, int cz) {
+    return (cx * cx + cy * cy + cz * cz) == 1 ? 1.0
+         : (cx * cx + cy * cy + cz * cz) == 2 ? 0.70710678118654752440
+         : (cx * cx + cy * cy + cz * cz) == 3 ? 0.57735026918962576451 : 0.0;
+}
+
+// Pass 1 of the two-component adjoint step at source node y: writes the
+// cotangents of y's 11 fields (before the phase-field chain) to lam and of
+// G(y) to lam_g (3 fields), and the block's dL/domega to domega_rows.
+template <class L, class T>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_cg_local(const T* __restrict__ lam_new,
+                                                                  const T* __restrict__ m, T* __restrict__ lam,
+                                                                  T* __restrict__ lam_g, Layout lay, CGAdjPar<T> p,
+                                                                  double* __restrict__ domega_rows) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const size_t fs = lay.fs;
+    double part = 0.0;
+    if (x < lay.nx) {
+        const size_t i0 = lay.at(x, y, z);
+        T s[11];
+#pragma unroll
+        for (int f = 0; f < 11; ++f) s[f] = m[f * fs + i0];
+        const T r1 = s[0], d = s[1], jx = s[2], jy = s[3], jz = s[4];
+        const T* A = s + 5;  // xx, yy, zz, xy, xz, yz
+        // G(y) from phi of the neighbours
+        T G[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+            for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+                for (int cx = -1; cx <= 1; ++cx) {
+                    if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0 && cz == 0)) continue;
+                    const size_t q = lay.at(wrap_idx(x + cx, lay.nx), wrap_idx(y + cy, lay.ny), wrap_idx(z + cz, lay.nz));
+                    const T ph = T(2) * m[q] / (T(1) + m[fs + q]) - T(1);
+                    const T wp = T(3.0 * L::w(cx, cy, cz)) * ph;
+                    G[0] += T(cx) * wp;
+                    G[1] += T(cy) * wp;
+                    G[2] += T(cz) * wp;
+                }
+        // forward quantities of the node
+        const T rho = T(1) + d, rinv = T(1) / rho, om = p.omega;
+        const T gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2] + p.eps2);
+        const T n[3] = {G[0] / gn, G[1] / gn, G[2] / gn};
+        const T ks = p.A_s * gn * T(1.0 / 9.0);
+        const T jj[6] = {jx * jx, jy * jy, jz * jz, jx * jy, jx * jz, jy * jz};
+        const T nn[6] = {n[0] * n[0], n[1] * n[1], n[2] * n[2], n[0] * n[1], n[0] * n[2], n[1] * n[2]};
+        T Ap[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Ap[k] = (T(1) - om) * A[k] + om * jj[k] * rinv + ks * nn[k];
+        const T s0 = d - T(1.5) * (Ap[0] + Ap[1] + Ap[2]);
+        const T r1r = r1 * rinv;
+        const T e = p.beta * r1 * (rho - r1) * rinv;
+        // pull transposed: per direction, the cotangents of g'_i and h1'_i
+        T ld = T(0), lj[3] = {T(0), T(0), T(0)}, la[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        T l_r1r = T(0), l_e = T(0), ln[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+            for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+                for (int cx = -1; cx <= 1; ++cx) {
+                    if (!L::has(cx, cy, cz)) continue;
+                    const size_t q = lay.at(wrap_idx(x + cx, lay.nx), wrap_idx(y + cy, lay.ny), wrap_idx(z + cz, lay.nz));
+                    T v[11];
+#pragma unroll
+                    for (int f = 0; f < 11; ++f) v[f] = lam_new[f * fs + q];
+                    const T cxx = T(cx * cx) - T(kCs2), cyy = T(cy * cy) - T(kCs2), czz = T(cz * cz) - T(kCs2);
+                    const T si = v[1] + T(cx) * v[2] + T(cy) * v[3] + T(cz) * v[4] + cxx * v[5] + cyy * v[6] +
+                                 czz * v[7] + T(cx * cy) * v[8] + T(cx * cz) * v[9] + T(cy * cz) * v[10];
+                    const T ti = v[0];
+                    const T w = T(L::w(cx, cy, cz));
+                    T qd = s0;
+                    if (cx) qd += T(4.5) * Ap[0];
+                    if (cy) qd += T(4.5) * Ap[1];
+                    if (cz) qd += T(4.5) * Ap[2];
+                    if (cx * cy) qd += T(9 * cx * cy) * Ap[3];
+                    if (cx * cz) qd += T(9 * cx * cz) * Ap[4];
+                    if (cy * cz) qd += T(9 * cy * cz) * Ap[5];
+                    const T gi = w * (qd + T(3 * cx) * jx + T(3 * cy) * jy + T(3 * cz) * jz);
+                    l_r1r += ti * (w + gi);
+                    if (cx || cy || cz) {
+                        const T il = T(inv_len_c(cx, cy, cz));
+                        const T cn = T(cx) * n[0] + T(cy) * n[1] + T(cz) * n[2];
+                        l_e += ti * w * cn * il;
+                        const T f = ti * e * w * il;
+                        ln[0] += f * T(cx);
+                        ln[1] += f * T(cy);
+                        ln[2] += f * T(cz);
+                    }
+                    const T ws = w * (si + ti * r1r);
+                    ld += ws;
+                    lj[0] += T(3 * cx) * ws;
+                    lj[1] += T(3 * cy) * ws;
+                    lj[2] += T(3 * cz) * ws;
+                    la[0] += (T(4.5 * cx * cx) - T(1.5)) * ws;
+                    la[1] += (T(4.5 * cy * cy) - T(1.5)) * ws;
+                    la[2] += (T(4.5 * cz * cz) - T(1.5)) * ws;
+                    la[3] += T(9 * cx * cy) * ws;
+                    la[4] += T(9 * cx * cz) * ws;
+                    la[5] += T(9 * cy * cz) * ws;
+                }
+        // collision transposed: A' = (1 - w) A + w j j / rho + ks n n
+        T l_rinv = T(0), l_ks = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            l_rinv += om * la[k] * jj[k];
+            l_ks += la[k] * nn[k];
+        }
+        T out[11];
+        out[2] = lj[0] + om * rinv * (T(2) * jx * la[0] + jy * la[3] + jz * la[4]);
+        out[3] = lj[1] + om * rinv * (T(2) * jy * la[1] + jx * la[3] + jz * la[5]);
+        out[4] = lj[2] + om * rinv * (T(2) * jz * la[2] + jx * la[4] + jy * la[5]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out[5 + k] = (T(1) - om) * la[k];
+        ln[0] += ks * (T(2) * n[0] * la[0] + n[1] * la[3] + n[2] * la[4]);
+        ln[1] += ks * (T(2) * n[1] * la[1] + n[0] * la[3] + n[2] * la[5]);
+        ln[2] += ks * (T(2) * n[2] * la[2] + n[0] * la[4] + n[1] * la[5]);
+        // ks = A_s gn / 9, n = G / gn, gn = sqrt(|G|^2 + eps^2)
+        T l_gn = p.A_s * T(1.0 / 9.0) * l_ks - (ln[0] * G[0] + ln[1] * G[1] + ln[2] * G[2]) / (gn * gn);
+        T lg[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lg[a] = ln[a] / gn + l_gn * G[a] / gn;
+        // colour split: r1r = r1 / rho, e = beta (r1 - r1^2 / rho)
+        l_rinv += l_r1r * r1 - l_e * p.beta * r1 * r1;
+        out[0] = l_r1r * rinv + l_e * p.beta * (T(1) - T(2) * r1 * rinv);
+        out[1] = ld - l_rinv * rinv * rinv;
+#pragma unroll
+        for (int f = 0; f < 11; ++f) lam[f * fs + i0] = out[f];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lam_g[a * fs + i0] = lg[a];
+        for (int k = 0; k < 6; ++k) part += (double)la[k] * ((double)jj[k] * (double)rinv - (double)A[k]);
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    __shared__ double wsum[kAdjThreads / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sacc = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) sacc += wsum[w];
+        const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        domega_rows[b] = sacc;
+    }
+}
+
+// Pass 2: the phase-field chain at node z.  G(y) = 3 sum_k w_k c_k phi(y + c_k)
+// transposed gives lam_phi(z) = 3 sum_k w_k c_k . lam_G(z - c_k); phi = 2 rho1 / rho - 1.
+template <class L, class T>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_cg_phi(const T* __restrict__ m, const T* __restrict__ lam_g,
+                                                                T* __restrict__ lam, Layout lay) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= lay.nx) return;
+    const size_t fs = lay.fs;
+    T lphi = T(0);
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx) {
+                if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0 && cz == 0)) continue;
+                const size_t q = lay.at(wrap_idx(x - cx, lay.nx), wrap_idx(y - cy, lay.ny), wrap_idx(z - cz, lay.nz));
+                lphi += T(3.0 * L::w(cx, cy, cz)) *
+                        (T(cx) * lam_g[q] + T(cy) * lam_g[fs + q] + T(cz) * lam_g[2 * fs + q]);
+            }
+    const size_t i0 = lay.at(x, y, z);
+    const T rinv = T(1) / (T(1) + m[fs + i0]);
+    lam[i0] += lphi * T(2) * rinv;
+    lam[fs + i0] -= lphi * T(2) * m[i0] * rinv * rinv;
+}
+
 // acc += sum of rows (one block, fixed order).
 __global__ void k_sum_rows(const double* __restrict__ rows, size_t n, double* __restrict__ acc) {
     __shared__ double sh[256];
@@ -160,6 +349,44 @@ __global__ void k_cot_shifted_to_canon(const T* __restrict__ lam, void* __restri
     }
 }
 
+// Two components: canonical (rho1, rho2, j, P) <-> internal (rho1, d, j, A) with
+// rho2 = 1 + d - rho1, P_aa = A_aa + cs^2 (1 + d); cotangents map by the transposes.
+template <class T>
+__global__ void k_cot2_canon_to_internal(const void* __restrict__ g, int dt, T* __restrict__ lam, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        double v[11];
+        for (int f = 0; f < 11; ++f)
+            v[f] = dt == LLB_F64 ? static_cast<const double*>(g)[f * N + i] : (double)static_cast<const float*>(g)[f * N + i];
+        const int x = (int)(i % L.nx);
+        const size_t r = i / L.nx;
+        const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
+        lam[j] = (T)(v[0] - v[1]);
+        lam[L.fs + j] = (T)(v[1] + kCs2 * (v[5] + v[6] + v[7]));
+        for (int f = 2; f < 11; ++f) lam[f * L.fs + j] = (T)v[f];
+    }
+}
+
+template <class T>
+__global__ void k_cot2_internal_to_canon(const T* __restrict__ lam, void* __restrict__ g, int dt, Layout L) {
+    const size_t N = (size_t)L.nx * L.ny * L.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % L.nx);
+        const size_t r = i / L.nx;
+        const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
+        double v[11];
+        for (int f = 0; f < 11; ++f) v[f] = (double)lam[f * L.fs + j];
+        const double tr = kCs2 * (v[5] + v[6] + v[7]);
+        const double g1 = v[0] + v[1] - tr, g2 = v[1] - tr;
+        v[0] = g1;
+        v[1] = g2;
+        for (int f = 0; f < 11; ++f) {
+            if (dt == LLB_F64) static_cast<double*>(g)[f * N + i] = v[f];
+            else static_cast<float*>(g)[f * N + i] = (float)v[f];
+        }
+    }
+}
+
 dim3 adj_grid(const llb_ctx& c) { return dim3((c.nx + kAdjThreads - 1) / kAdjThreads, c.ny, c.nz); }
 
 template <class L, class T>
@@ -178,6 +405,33 @@ cudaError_t adj_step(const llb_ctx& c, const void* lam_new, const void* m, void*
                                 : adj_step_t<D3Q27, float>(c, lam_new, m, lam, rows);
 }
 
+template <class L, class T>
+cudaError_t adj_cg_step_t(const llb_ctx& c, const void* lam_new, const void* m, void* lam, void* lam_g,
+                          double* rows) {
+    CGAdjPar<T> p;
+    p.omega = (T)c.omega;
+    p.beta = (T)c.params.beta;
+    p.A_s = (T)c.params.A_s;
+    p.eps2 = (T)(c.params.grad_eps * c.params.grad_eps);
+    k_adjoint_cg_local<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(
+        static_cast<const T*>(lam_new), static_cast<const T*>(m), static_cast<T*>(lam), static_cast<T*>(lam_g), c.lay,
+        p, rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adjoint_cg_phi<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(static_cast<const T*>(m),
+                                                                       static_cast<const T*>(lam_g),
+                                                                       static_cast<T*>(lam), c.lay);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_cg_step(const llb_ctx& c, const void* lam_new, const void* m, void* lam, void* lam_g, double* rows) {
+    if (c.Q == 19)
+        return c.storage == LLB_F64 ? adj_cg_step_t<D3Q19, double>(c, lam_new, m, lam, lam_g, rows)
+                                    : adj_cg_step_t<D3Q19, float>(c, lam_new, m, lam, lam_g, rows);
+    return c.storage == LLB_F64 ? adj_cg_step_t<D3Q27, double>(c, lam_new, m, lam, lam_g, rows)
+                                : adj_cg_step_t<D3Q27, float>(c, lam_new, m, lam, lam_g, rows);
+}
+
 int grid_n(const llb_ctx& c) {
     const size_t want = (c.N + 255) / 256;
     const size_t cap = (size_t)(c.num_sms > 0 ? c.num_sms : 148) * 8;
@@ -188,7 +442,8 @@ int grid_n(const llb_ctx& c) {
 cudaError_t fwd_one(llb_ctx* c) {
     const void* in = c->buf[c->cur];
     void* out = c->buf[1 - c->cur];
-    const cudaError_t e = c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, c->cur, out)
+    const cudaError_t e = c->ncomp == 2                   ? launch_cg_tiled(*c, in, out)
+                          : c->kernel == LLB_KERNEL_TMA   ? launch_moment_tma(*c, c->cur, out)
                           : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
                                                           : launch_moment_direct(*c, in, out);
     if (e == cudaSuccess) c->cur = 1 - c->cur;
@@ -203,10 +458,12 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     using namespace llb;
     if (!c) return LLB_EINVAL;
     if (c->sticky != LLB_OK) return LLB_ESTATE;
-    if (c->in_batch || c->scheme != LLB_SCHEME_MOMENT || c->ncomp != 1 ||
-        (c->storage != LLB_F32 && c->storage != LLB_F64) || nsteps < 0 || !dev_gfinal || !dev_ginit ||
-        (dtype != LLB_F64 && dtype != LLB_F32))
+    if (c->in_batch || c->scheme != LLB_SCHEME_MOMENT || (c->storage != LLB_F32 && c->storage != LLB_F64) ||
+        nsteps < 0 || !dev_gfinal || !dev_ginit || (dtype != LLB_F64 && dtype != LLB_F32))
         return LLB_EINVAL;
+    // two components: differentiable only without the near-contact switch and with the smooth normal
+    const bool two = c->ncomp == 2;
+    if (two && (c->params.A_h != 0.0 || !(c->params.grad_eps > 0.0))) return LLB_EINVAL;
     const int K = every > 0 ? every : (int)std::fmax(1.0, std::round(std::sqrt((double)nsteps)));
     const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
     const size_t sb = c->state_bytes;
@@ -231,9 +488,10 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     char* seg = static_cast<char*>(grab(sb * (size_t)K));
     void* lamA = grab(sb);
     void* lamB = grab(sb);
+    void* lamG = two ? grab(sb) : lamA;  // cotangent of G (3 fields), two components only
     double* rows = static_cast<double*>(grab(nrows * sizeof(double)));
     double* acc = static_cast<double*>(grab(sizeof(double)));
-    if (!ck || !seg || !lamA || !lamB || !rows || !acc) {
+    if (!ck || !seg || !lamA || !lamB || !lamG || !rows || !acc) {
         release();
         return LLB_ENOMEM;
     }
@@ -248,7 +506,11 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     }
     // cotangent of the final state
     if (e == cudaSuccess) {
-        if (c->storage == LLB_F64)
+        if (two && c->storage == LLB_F64)
+            k_cot2_canon_to_internal<double><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<double*>(lamA), c->lay);
+        else if (two)
+            k_cot2_canon_to_internal<float><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<float*>(lamA), c->lay);
+        else if (c->storage == LLB_F64)
             k_cot_canon_to_shifted<double><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<double*>(lamA), c->lay);
         else
             k_cot_canon_to_shifted<float><<<grid_n(*c), 256, 0, c->stream>>>(dev_gfinal, dtype, static_cast<float*>(lamA), c->lay);
@@ -265,7 +527,8 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
             if (e == cudaSuccess && s + 1 < s1) e = fwd_one(c);
         }
         for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
-            e = adj_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, rows);
+            e = two ? adj_cg_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, lamG, rows)
+                    : adj_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, rows);
             if (e == cudaSuccess) {
                 k_sum_rows<<<1, 256, 0, c->stream>>>(rows, nrows, acc);
                 e = cudaGetLastError();
@@ -277,7 +540,11 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     }
     // cotangent of the initial state, in canonical form
     if (e == cudaSuccess) {
-        if (c->storage == LLB_F64)
+        if (two && c->storage == LLB_F64)
+            k_cot2_internal_to_canon<double><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const double*>(lam_in), dev_ginit, dtype, c->lay);
+        else if (two)
+            k_cot2_internal_to_canon<float><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const float*>(lam_in), dev_ginit, dtype, c->lay);
+        else if (c->storage == LLB_F64)
             k_cot_shifted_to_canon<double><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const double*>(lam_in), dev_ginit, dtype, c->lay);
         else
             k_cot_shifted_to_canon<float><<<grid_n(*c), 256, 0, c->stream>>>(static_cast<const float*>(lam_in), dev_ginit, dtype, c->lay);

@@ -80,6 +80,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     if (p.ncomp == 2 && p.variant > 1) { *why = "the two-component kernel has variants 0..1"; return LLB_EINVAL; }
     if (p.wait_budget_ms < 1 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 1..600000"; return LLB_EINVAL; }
     if (p.debug_flags & ~1) { *why = "unknown debug flag"; return LLB_EINVAL; }
+    if (!(p.grad_eps >= 0.0) || !std::isfinite(p.grad_eps)) { *why = "grad_eps must be finite and >= 0"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
         if (p.scheme != LLB_SCHEME_MOMENT) { *why = "two components run only the moment-only scheme"; return LLB_EINVAL; }
         if (nx < 4 || ny < 4 || nz < 4) { *why = "two components need nx, ny, nz >= 4"; return LLB_EINVAL; }
@@ -239,6 +240,7 @@ void llb_params_default(llb_params* p) {
     p->stream = nullptr;
     p->buffers[0] = p->buffers[1] = nullptr;
     p->wait_budget_ms = 2000;
+    p->grad_eps = 0.0;
 }
 
 int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p, llb_footprint* out) {

@@ -4,7 +4,8 @@
 // State per node (11 fields): rho1, d = rho - 1 (total density), j, A = P - cs^2 rho I.
 // Per source node y (tile plus one-node halo), from the moments at time t:
 //   phi = (rho1 - rho2) / rho = 2 rho1 / rho - 1              (Sec. III B)
-//   G = (1/cs^2) sum_k w_k c_k phi(y + c_k), n = G / |G| (0 if |G| < g_min)
+//   G = (1/cs^2) sum_k w_k c_k phi(y + c_k), n = G / |G| (0 if |G| < g_min);
+//   with grad_eps > 0, |G| is the smooth sqrt(|G|^2 + eps^2) and n = G / |G| everywhere
 //   near contact: |G| >= g_nci and phi(y + round(k n_out)) > phi(y) + 0.01 for
 //   some k = 1..h_c, n_out = -n; then F = A_h G (F_rep = -A_h n_out delta_I,
 //   delta_I = |G|), else F = 0
@@ -42,6 +43,7 @@ constexpr double kGNci = 0.05;     // |grad phi| above which a node is in the de
 template <class T>
 struct CGPar {
     T omega, beta, A_s, A_h, g_min, g_nci;
+    T eps2;  // > 0: smooth norm |G|_eps = sqrt(|G|^2 + eps2), normal defined everywhere
     int h_c;
 };
 
@@ -166,10 +168,12 @@ __device__ __forceinline__ Src2<T> collide2(const Node2<T>& a, const T* __restri
                 if (cz) Gz += T(cz) * wd;
             }
     const T g2 = Gx * Gx + Gy * Gy + Gz * Gz;
-    const T gn = sqrt(g2);
+    const bool smooth = p.eps2 > T(0);
+    const T gn = sqrt(smooth ? g2 + p.eps2 : g2);
+    const bool has_n = smooth || gn >= p.g_min;
     Src2<T> s;
     s.nx = s.ny = s.nz = T(0);
-    if (gn >= p.g_min) {
+    if (has_n) {
         const T ig = T(1) / gn;
         s.nx = Gx * ig;
         s.ny = Gy * ig;
@@ -197,7 +201,7 @@ __device__ __forceinline__ Src2<T> collide2(const Node2<T>& a, const T* __restri
     const T rinv = T(1) / rho;
     const T ux = (m.jx + T(0.5) * Fx) * rinv, uy = (m.jy + T(0.5) * Fy) * rinv, uz = (m.jz + T(0.5) * Fz) * rinv;
     const T om = p.omega, one_m = T(1) - om, fh = T(1) - T(0.5) * om;
-    const T ks = gn >= p.g_min ? p.A_s * gn * T(1.0 / 9.0) : T(0);
+    const T ks = has_n ? p.A_s * gn * T(1.0 / 9.0) : T(0);
     const T orx = om * rho * ux, ory = om * rho * uy, orz = om * rho * uz;
     s.c.d = m.d;
     s.c.jx = m.jx + Fx;
@@ -582,6 +586,7 @@ cudaError_t cg_run_v(const llb_ctx& c, const void* in, void* out) {
     p.A_h = (T)c.params.A_h;
     p.g_min = (T)c.params.g_min;
     p.g_nci = (T)kGNci;
+    p.eps2 = (T)(c.params.grad_eps * c.params.grad_eps);
     p.h_c = c.params.h_c;
     k_cg_tiled<L, T, kBX2, kBY2><<<grid, C::NT, C::smem_bytes, c.stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), c.lay, p, sc);
@@ -620,6 +625,7 @@ cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int
     p.A_h = (T)c.params.A_h;
     p.g_min = (T)c.params.g_min;
     p.g_nci = (T)kGNci;
+    p.eps2 = (T)(c.params.grad_eps * c.params.grad_eps);
     p.h_c = c.params.h_c;
     k_cg_batch<L, T, kBX2, kBY2><<<grid, C::NT, C::smem_bytes, c.stream>>>(doms, ndom, total, p);
     return cudaGetLastError();

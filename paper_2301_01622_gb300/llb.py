@@ -31,7 +31,7 @@ class llb_params(C.Structure):
         ("ncomp", C.c_int), ("storage", C.c_int), ("scheme", C.c_int), ("kernel", C.c_int), ("variant", C.c_int),
         ("beta", C.c_double), ("A_s", C.c_double), ("A_h", C.c_double), ("g_min", C.c_double),
         ("h_c", C.c_int), ("stream", C.c_void_p), ("buffers", C.c_void_p * 2), ("wait_budget_ms", C.c_int),
-        ("debug_flags", C.c_int),
+        ("debug_flags", C.c_int), ("grad_eps", C.c_double),
     ]
 
 

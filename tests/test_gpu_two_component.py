@@ -163,3 +163,17 @@ def test_near_contact_force_outcome(A_h, expect):
     assert (gap_min < -0.9) if expect == 2 else (gap_min > 0.9)
     for k in range(2):
         assert abs(d1["mass"][k] - d0["mass"][k]) < 1e-5 * d0["mass"][k]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_smooth_normal_matches_oracle(q):
+    """Smooth interface normal (grad_eps > 0): FP64 within 1e-12 and FP32
+    within 1e-5 of the oracle's smooth form, nearly touching off-axis pair."""
+    shape, steps, tau = (40, 24, 20), 20, 0.9
+    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, eps=0.02)
+    ref = tc.run_moment_only(_moments(r1, r2, u), LAT[q], tau, prm, steps)
+    for storage, tol in ((llb.LLB_F64, 1e-12), (llb.LLB_F32, 1e-5)):
+        got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, ncomp=2, storage=storage,
+                         beta=0.7, A_s=0.02, A_h=0.0, grad_eps=0.02)
+        assert_groups(got, ref, tol, GROUPS_2, what=f"D3Q{q} smooth storage {storage}")
