@@ -2,7 +2,10 @@
 
 ``evolve(m0, tau, nsteps)`` advances canonical moments m0 (a CUDA tensor of
 shape (10, nz, ny, nx), float64 or float32) by nsteps one-component steps
-through libllb and returns the canonical moments at the end.  Its backward
+through libllb and returns the canonical moments at the end; with
+``two_component=dict(beta=..., A_s=..., grad_eps=...)`` m0 has the 11
+two-component fields (rho1, rho2, j, P) and the colour-gradient step with the
+smooth interface normal (no near-contact switch) is used.  Its backward
 pass calls ``llb_adjoint`` (hand-written adjoint kernels with checkpoints of
 the moments every ``every`` steps), so gradients of any torch loss of the
 result flow to m0 -- and through whatever built m0, e.g. an equilibrium
@@ -17,20 +20,23 @@ import torch
 from . import llb
 
 
-def _params(dtype, stream):
+def _params(dtype, stream, cg):
     storage = llb.LLB_F64 if dtype == torch.float64 else llb.LLB_F32
-    return llb.llb_params_default(storage=storage, stream=stream)
+    if cg is None:
+        return llb.llb_params_default(storage=storage, stream=stream)
+    return llb.llb_params_default(storage=storage, stream=stream, ncomp=2, A_h=0.0, **cg)
 
 
 class MomentOnlyEvolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, m0, tau, nsteps: int, lattice: int, every: int):
-        if not m0.is_cuda or m0.dim() != 4 or m0.shape[0] != 10:
-            raise ValueError("m0 must be a CUDA tensor of shape (10, nz, ny, nx)")
+    def forward(ctx, m0, tau, nsteps: int, lattice: int, every: int, cg):
+        nf = 10 if cg is None else 11
+        if not m0.is_cuda or m0.dim() != 4 or m0.shape[0] != nf:
+            raise ValueError(f"m0 must be a CUDA tensor of shape ({nf}, nz, ny, nx)")
         m0c = m0.detach().contiguous()
         nz, ny, nx = m0c.shape[1:]
         stream = torch.cuda.current_stream().cuda_stream
-        c = llb.llb_create(nx, ny, nz, lattice, float(tau), _params(m0c.dtype, stream))
+        c = llb.llb_create(nx, ny, nz, lattice, float(tau), _params(m0c.dtype, stream, cg))
         try:
             llb.llb_init_moments_device(c, m0c)
             llb.llb_step(c, nsteps)
@@ -40,7 +46,7 @@ class MomentOnlyEvolve(torch.autograd.Function):
         finally:
             llb.llb_destroy(c)
         ctx.save_for_backward(m0c)
-        ctx.tau, ctx.nsteps, ctx.lattice, ctx.every = float(tau), nsteps, lattice, every
+        ctx.tau, ctx.nsteps, ctx.lattice, ctx.every, ctx.cg = float(tau), nsteps, lattice, every, cg
         ctx.tau_shape = tau.shape if isinstance(tau, torch.Tensor) else None
         return out
 
@@ -49,7 +55,7 @@ class MomentOnlyEvolve(torch.autograd.Function):
         (m0c,) = ctx.saved_tensors
         nz, ny, nx = m0c.shape[1:]
         stream = torch.cuda.current_stream().cuda_stream
-        c = llb.llb_create(nx, ny, nz, ctx.lattice, ctx.tau, _params(m0c.dtype, stream))
+        c = llb.llb_create(nx, ny, nz, ctx.lattice, ctx.tau, _params(m0c.dtype, stream, ctx.cg))
         try:
             llb.llb_init_moments_device(c, m0c)
             ginit = torch.empty_like(m0c)
@@ -59,11 +65,13 @@ class MomentOnlyEvolve(torch.autograd.Function):
         gtau = None
         if ctx.tau_shape is not None:
             gtau = torch.full(ctx.tau_shape, dtau, dtype=torch.float64, device=m0c.device)
-        return ginit, gtau, None, None, None
+        return ginit, gtau, None, None, None, None
 
 
-def evolve(m0: torch.Tensor, tau, nsteps: int, lattice: int = 19, every: int = 0) -> torch.Tensor:
+def evolve(m0: torch.Tensor, tau, nsteps: int, lattice: int = 19, every: int = 0,
+           two_component: dict | None = None) -> torch.Tensor:
     """Differentiable nsteps moment-only steps of canonical moments m0 (see module doc)."""
     if not isinstance(tau, torch.Tensor):
         tau = torch.tensor(float(tau), dtype=torch.float64)
-    return MomentOnlyEvolve.apply(m0, tau, int(nsteps), int(lattice), int(every))
+    cg = dict(two_component) if two_component is not None else None
+    return MomentOnlyEvolve.apply(m0, tau, int(nsteps), int(lattice), int(every), cg)

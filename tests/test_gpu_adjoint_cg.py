@@ -133,3 +133,19 @@ def test_adjoint_requires_smooth_normal_and_no_switch():
             assert e.value.status == llb.LLB_EINVAL
         finally:
             llb.llb_destroy(ctx)
+
+
+def test_autograd_wrapper_two_components(case):
+    """torch.autograd through evolve(..., two_component=...) gives the same
+    initial-moment gradient and dL/dtau as the direct adjoint call."""
+    from paper_2301_01622_gb300.autograd import evolve
+    m0, target, _, g0, dtau, _ = case
+    m = torch.from_numpy(m0).cuda().requires_grad_(True)
+    tau = torch.tensor(TAU, dtype=torch.float64, requires_grad=True)
+    cg = dict(beta=PRM["beta"], A_s=PRM["A_s"], grad_eps=PRM["grad_eps"])
+    mN = evolve(m, tau, STEPS, lattice=27, every=5, two_component=cg)
+    phi = (mN[0] - mN[1]) / (mN[0] + mN[1])
+    L = ((phi - torch.from_numpy(target).cuda()) ** 2).sum()
+    L.backward()
+    np.testing.assert_allclose(m.grad.cpu().numpy(), g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+    assert abs(float(tau.grad) - dtau) <= 1e-9 * abs(dtau)
