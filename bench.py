@@ -264,6 +264,7 @@ def gpu_arm(args, rank, world, local):
     if not args.no_extra:
         extra["two_component_d3q27"] = droplet_arm(args, llb, inputs, stream, world, peak)
         extra["batched_ensemble"] = ensemble_arm(args, llb, inputs, stream, world, peak)
+        extra["adjoint_two_component_d3q27"] = adjoint_arm(args, llb, inputs, stream, world)
 
     # end to end through the C ABI with pinned host buffers
     e2e = e2e_arm(args, llb, rho, u, stream, world)
@@ -346,6 +347,36 @@ def ensemble_arm(args, llb, inputs, stream, world, peak):
     return {"mlups": world * nodes / t / 1e6, "frac": gbs / peak, "achieved_gbs": gbs, "bytes_per_node": 88,
             "ms_per_step": ms / steps, "steps": steps, "boxes": 64, "nodes": nodes, "variant": variant,
             "workload": "64 two-component D3Q27 droplet boxes, sizes from {48,64,96,128}^3, one launch per step, CUDA graph"}
+
+
+def adjoint_arm(args, llb, inputs, stream, world):
+    """Gradient of a phase-field mismatch loss through 500 two-component D3Q27
+    FP32 steps on 96^3 (off-axis droplet pair, smooth interface normal, no
+    near-contact switch), checkpoints every 22 steps: one llb_adjoint call
+    (forward with checkpoints, segment recomputation, adjoint steps)."""
+    import torch
+    n, steps, every = 96, 500, 22
+    prm = dict(ncomp=2, storage=llb.LLB_F32, beta=0.7, A_s=0.01, A_h=0.0, grad_eps=0.02, stream=stream)
+    r1, r2, u = inputs.droplet_pair(n, n, n, 12.0, 0.05, 6.0)
+    ctx = llb.llb_create(n, n, n, 27, 1.0, llb.llb_params_default(**prm))
+    try:
+        llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
+        g = torch.zeros((11, n, n, n), dtype=torch.float32, device="cuda")
+        g[0] = 1e-3
+        gi = torch.empty_like(g)
+        llb.llb_adjoint(ctx, 10, g, gi, every=5)   # warm-up (allocations, first launches)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        llb.llb_adjoint(ctx, steps, g, gi, every=every)   # synchronises
+        dt = reduce_max(time.perf_counter() - t0, world)
+    finally:
+        llb.llb_destroy(ctx)
+    nodes = n ** 3
+    return {"seconds": dt, "steps": steps, "checkpoint_every": every,
+            "mlups_gradient": world * nodes * steps / dt / 1e6,
+            "workload": "96^3 D3Q27 two-component FP32, 500 steps, loss gradient w.r.t. initial moments and tau "
+                        "(forward + recomputation + adjoint per step; host wall clock of one synchronising call)"}
 
 
 def e2e_arm(args, llb, rho, u, stream, world):
