@@ -533,6 +533,7 @@ def main():
         "population_d3q27": _short(extra.get("population_d3q27")),
         "two_component_d3q27": extra.get("two_component_d3q27"),
         "batched_ensemble": extra.get("batched_ensemble"),
+        "adjoint_two_component_d3q27": extra.get("adjoint_two_component_d3q27"),
         "speedup_vs_population_d3q19": (main_r["mlups"] / extra["population_d3q19"]["mlups"])
         if "population_d3q19" in extra else None,
         "diagnostics": diag,
