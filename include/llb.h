@@ -95,9 +95,10 @@ typedef struct llb_params {
     int storage;      /* LLB_F32 (default), LLB_F64, LLB_F16S, LLB_BF16S     */
     int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
     int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
-    int variant;      /* tuning variant, 0 = default: tiled kernel 0..7
+    int variant;      /* tuning variant, 0 = default: tiled kernel 0..9
                          (tile shape, CTAs per SM, split-phase plane
-                         barrier, IEEE or approximate FP32 1/rho), TMA
+                         barrier, IEEE or approximate FP32 1/rho, dedicated
+                         halo warps), TMA
                          kernel 0..4, two
                          components 0..1; a variant the kernel does not have
                          is LLB_EINVAL.  Every variant computes the same

@@ -76,7 +76,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
         p.kernel != LLB_KERNEL_TMA) {
         *why = "unknown kernel"; return LLB_EINVAL;
     }
-    if (p.variant < 0 || p.variant > 7) { *why = "variant must be in 0..7"; return LLB_EINVAL; }
+    if (p.variant < 0 || p.variant > 9) { *why = "variant must be in 0..9"; return LLB_EINVAL; }
     if (p.ncomp == 2 && p.variant > 1) { *why = "the two-component kernel has variants 0..1"; return LLB_EINVAL; }
     if (p.wait_budget_ms < 1 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 1..600000"; return LLB_EINVAL; }
     if (p.debug_flags & ~1) { *why = "unknown debug flag"; return LLB_EINVAL; }
@@ -460,9 +460,9 @@ int llb_autotune(llb_ctx* c, int trials, int* kernel, int* variant) {
         return LLB_OK;
     }
     struct Cand { int kernel, variant; };
-    Cand cands[16];
+    Cand cands[24];
     int nc = 0;
-    const int nvar = c->ncomp == 2 ? 2 : 8;
+    const int nvar = c->ncomp == 2 ? 2 : 10;
     for (int v = 0; v < nvar; ++v) cands[nc++] = {LLB_KERNEL_TILED, v};
     if (c->ncomp == 1) {
         for (int v = 0; v < 5; ++v) cands[nc++] = {LLB_KERNEL_TMA, v};

@@ -349,7 +349,10 @@ __device__ __forceinline__ void publish_halo(T* __restrict__ G, int n, int role,
 //               finished one step earlier while the others catch up, and only
 //               then waits (bounded) before pulling; replaces __syncthreads.
 //   kFastRcp -- FP32 collision with the approximate division for 1/rho.
-constexpr int kSplit = 1, kFastRcp = 2;
+//   kHaloWarps -- two extra warps collide and publish the halo ring of the
+//               tile (top row, bottom row, side columns and corners) so that
+//               every output warp does the same work per plane (BX = 64).
+constexpr int kSplit = 1, kFastRcp = 2, kHaloWarps = 4;
 
 template <class L, class T, int BX, int BY>
 struct Tiled {
@@ -481,6 +484,135 @@ __global__ void __launch_bounds__(BX * BY, MINB)
             ++s;
             if (!plane_step(s, a2, a0, a1)) return;
             if (s == zb) { last(a2); break; }
+            ++s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled z-marching kernel with dedicated halo warps (kHaloWarps).  Threads
+// [0, BX BY) own the output columns; the 64 threads after them (two warps)
+// collide the halo ring of every source plane: thread h takes top-row node
+// h, bottom-row node h and, for h < 2 BY + 4, one side-column or corner
+// node.  Both groups pass the same barrier once per plane; since the
+// exchange buffer is double-buffered, the halo warps may run one plane ahead
+// of the output warps' pulls.
+template <class L, class T, int BX, int BY, int MINB, int OPT, class S>
+__global__ void __launch_bounds__(BX * BY + 64, MINB)
+    k_moment_tiled_hw(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc) {
+    static_assert(BX == 64, "the halo warps take one top-row and one bottom-row node per thread");
+    using K = Tiled<L, T, BX, BY>;
+    constexpr int HX = K::HX, HN = K::HN, NS = K::NS, NO = BX * BY;
+    constexpr bool FAST = (OPT & kFastRcp) != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const Gbase = reinterpret_cast<T*>(smem_raw);
+    const int nx = lay.nx, ny = lay.ny, nz = lay.nz;
+    const size_t plane = (size_t)lay.px * lay.py;
+
+    const int t = threadIdx.x;
+    const bool outw = t < NO;  // warp-uniform: NO is a multiple of 32
+    const int h = t - NO;
+    // output role
+    const int tx = t % BX, ty = t / BX;
+    const int n1 = (ty + 1) * HX + (tx + 1);
+    // halo role: top node (h + 1, 0), bottom node (h + 1, BY + 1), side / corner node
+    int hxc = 0, hyc = 0;
+    const bool hasc = !outw && h < 2 * BY + 4;
+    if (hasc) {
+        if (h < BY) { hxc = 0; hyc = h + 1; }
+        else if (h < 2 * BY) { hxc = BX + 1; hyc = h - BY + 1; }
+        else {
+            const int k = h - 2 * BY;
+            hxc = (k & 1) ? BX + 1 : 0;
+            hyc = (k & 2) ? BY + 1 : 0;
+        }
+    }
+    const int nA = h + 1, nB = (BY + 1) * HX + h + 1, nC = hyc * HX + hxc;
+    int buf = 0;
+
+    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
+        int x0, y0, za, zb;
+        sc.item(it, BX, BY, nz, x0, y0, za, zb);
+        // per-thread base pointers (plane 0) of up to three source nodes
+        const S* pA;
+        const S* pB = in;
+        const S* pC = in;
+        if (outw) {
+            pA = in + lay.at(pmod(x0 + tx, nx), pmod(y0 + ty, ny), 0);
+        } else {
+            pA = in + lay.at(pmod(x0 + h, nx), pmod(y0 - 1, ny), 0);
+            pB = in + lay.at(pmod(x0 + h, nx), pmod(y0 + BY, ny), 0);
+            if (hasc) pC = in + lay.at(pmod(x0 - 1 + hxc, nx), pmod(y0 - 1 + hyc, ny), 0);
+        }
+        const int ox = x0 + tx, oy = y0 + ty;
+        const bool store_ok = outw && (ox < nx) && (oy < ny);
+        const bool ghost = store_ok && lay.ghosts &&
+                           (ox < kGhostX || ox >= nx - kGhostX || oy < lay.yo || oy >= ny - lay.yo);
+        S* out1 = out + (store_ok ? lay.at(ox, oy, za) : 0);
+
+        int zn = pmod(za - 1, nz);
+        size_t zn_off = (size_t)zn * plane;
+        Mom<T> mA = load_mom<T>(pA + zn_off, 0, lay.fs);
+        Mom<T> mB, mC;
+        if (!outw) mB = load_mom<T>(pB + zn_off, 0, lay.fs);
+        if (hasc) mC = load_mom<T>(pC + zn_off, 0, lay.fs);
+
+        Acc<T> a0, a1, a2;
+        a0.zero(); a1.zero(); a2.zero();
+
+        auto plane_step = [&](int s, Acc<T>& X, Acc<T>& Y, Acc<T>& Z) {
+            T* const G = Gbase + buf * (NS * HN);
+            const bool more = s + 1 <= zb;
+            if (more) {
+                if (++zn == nz) {
+                    zn = 0;
+                    zn_off = 0;
+                } else {
+                    zn_off += plane;
+                }
+            }
+            T g_m = T(0), g_0 = T(0), g_p = T(0);
+            if (outw) {
+                const Mom<T> c1 = collide<T, FAST>(mA, omega);
+                if (more) mA = load_mom<T>(pA + zn_off, 0, lay.fs);
+                publish<L, T, HN>(G, n1, c1);
+                own_column<L, T>(c1, g_m, g_0, g_p);
+            } else {
+                const Mom<T> cA = collide<T, FAST>(mA, omega);
+                if (more) mA = load_mom<T>(pA + zn_off, 0, lay.fs);
+                publish<L, T, HN, kAny, 1>(G, nA, cA);
+                const Mom<T> cB = collide<T, FAST>(mB, omega);
+                if (more) mB = load_mom<T>(pB + zn_off, 0, lay.fs);
+                publish<L, T, HN, kAny, -1>(G, nB, cB);
+                if (hasc) {
+                    const Mom<T> cC = collide<T, FAST>(mC, omega);
+                    if (more) mC = load_mom<T>(pC + zn_off, 0, lay.fs);
+                    publish<L, T, HN>(G, nC, cC);
+                }
+            }
+            __syncthreads();
+            if (outw) {
+                gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
+                if (s - 1 >= za && store_ok) {
+                    const Mom<T> r = X.finish();
+                    store_mom(out1, 0, lay.fs, r);
+                    if (ghost) store_node(out, lay, ox, oy, s - 1, r);
+                    out1 += plane;
+                }
+            }
+            buf ^= 1;
+        };
+
+        int s = za - 1;
+        for (;;) {
+            if (s > zb) break;
+            plane_step(s, a0, a1, a2);
+            ++s;
+            if (s > zb) break;
+            plane_step(s, a1, a2, a0);
+            ++s;
+            if (s > zb) break;
+            plane_step(s, a2, a0, a1);
             ++s;
         }
     }
@@ -692,16 +824,32 @@ template <> struct TiledVariant<float, 4> { using type = TiledShape<128, 4, 1, k
 template <> struct TiledVariant<float, 5> { using type = TiledShape<64, 4, 2>; };
 template <> struct TiledVariant<float, 6> { using type = TiledShape<64, 4, 2, kSplit | kFastRcp>; };
 template <> struct TiledVariant<float, 7> { using type = TiledShape<32, 4, 4, kFastRcp>; };
+// halo-warp forms: 16 warps per SM in total keep 128 registers per thread
+template <> struct TiledVariant<float, 8> { using type = TiledShape<64, 7, 1, kFastRcp | kHaloWarps>; };
+template <> struct TiledVariant<float, 9> { using type = TiledShape<64, 3, 2, kFastRcp | kHaloWarps>; };
 template <int V> struct TiledVariant<double, V> { using type = TiledShape<32, 8, 1>; };
+
+// Threads of a CTA of tile shape S (the halo-warp form adds two warps).
+template <class S>
+constexpr int tiled_threads() { return S::BX * S::BY + ((S::OPT & kHaloWarps) ? 64 : 0); }
+
+template <class L, class T, class St, class S>
+auto tiled_kernel() {
+    if constexpr ((S::OPT & kHaloWarps) != 0)
+        return k_moment_tiled_hw<L, T, S::BX, S::BY, S::MINB, S::OPT, St>;
+    else
+        return k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St>;
+}
 
 template <class L, class T, class St, class S>
 int tiled_ctas_c(const llb_ctx& c) {
     using K = Tiled<L, T, S::BX, S::BY>;
-    auto kern = k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St>;
+    auto kern = tiled_kernel<L, T, St, S>();
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::NT, K::smem_bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tiled_threads<S>(), K::smem_bytes) !=
+            cudaSuccess ||
         per_sm < 1)
         return 0;
     const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, per_sm * c.num_sms);
@@ -715,9 +863,14 @@ cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
     const Sched sc = plan(c.nx, c.ny, c.nz, S::BX, S::BY, grid);
     // device clock ~2 GHz: cycles per millisecond
     const long long budget = (long long)c.params.wait_budget_ms * 2000000LL;
-    k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St><<<grid, K::NT, K::smem_bytes, c.stream>>>(
-        static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc, static_cast<int*>(c.err_dev),
-        budget);
+    if constexpr ((S::OPT & kHaloWarps) != 0)
+        k_moment_tiled_hw<L, T, S::BX, S::BY, S::MINB, S::OPT, St><<<grid, tiled_threads<S>(), K::smem_bytes,
+                                                                      c.stream>>>(
+            static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc);
+    else
+        k_moment_tiled<L, T, S::BX, S::BY, S::MINB, S::OPT, St><<<grid, K::NT, K::smem_bytes, c.stream>>>(
+            static_cast<const St*>(in), static_cast<St*>(out), c.lay, (T)c.omega, sc, static_cast<int*>(c.err_dev),
+            budget);
     return cudaGetLastError();
 }
 
@@ -730,6 +883,8 @@ cudaError_t run_tiled_c(const llb_ctx& c, const void* in, void* out) {
         case 5: return fn<L, T, St, typename TiledVariant<T, 5>::type>(__VA_ARGS__);         \
         case 6: return fn<L, T, St, typename TiledVariant<T, 6>::type>(__VA_ARGS__);         \
         case 7: return fn<L, T, St, typename TiledVariant<T, 7>::type>(__VA_ARGS__);         \
+        case 8: return fn<L, T, St, typename TiledVariant<T, 8>::type>(__VA_ARGS__);         \
+        case 9: return fn<L, T, St, typename TiledVariant<T, 9>::type>(__VA_ARGS__);         \
         default: return fn<L, T, St, typename TiledVariant<T, 0>::type>(__VA_ARGS__);        \
     }
 

@@ -96,7 +96,7 @@ def _oracle_ragged(q):
     return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
 
 
-KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(8)]
+KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(10)]
 
 
 @pytest.mark.parametrize("kernel, variant", KERNEL_VARIANTS,
@@ -104,7 +104,7 @@ KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL
 @pytest.mark.parametrize("q", [19, 27])
 def test_kernel_variants_match_oracle(variant, kernel, q):
     """Every tuning variant of the z-marching kernels (tile shape, ring depth,
-    CTAs/SM, split-phase plane barrier, approximate 1/rho) computes the same
+    CTAs/SM, split-phase plane barrier, approximate 1/rho, halo warps) computes the same
     step: ragged multi-tile box, FP32, 1e-5 after 20 steps."""
     shape = (133, 37, 29)
     rho, u = inputs.taylor_green_3d(*shape, u0=0.05, noise=1e-3, seed=7)
@@ -119,7 +119,7 @@ def test_kernel_variants_match_oracle(variant, kernel, q):
 
 
 def test_tma_kernel_has_five_variants():
-    """Variants 5..7 exist for the plain-load kernel only: asking the TMA
+    """Variants 5..9 exist for the plain-load kernel only: asking the TMA
     kernel for one is refused at creation."""
     p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, variant=5)
     with pytest.raises(llb.LLBError) as e:
