@@ -3,7 +3,7 @@
 Workload (one step = one full time step of the hot path over the box):
 256^3 periodic box, D3Q19, FP32 moments, 3D Taylor-Green vortex u0 = 0.05
 plus seeded U(-1e-3, 1e-3) velocity noise, tau = 0.6.  Metric: MLUPS =
-nodes / (1e6 * seconds per step) (Sec. III C, Eq. mlups), with the HBM
+nodes / (1e6 * seconds per step) (Sec. IV A, Eq. (12)), with the HBM
 roofline fraction of the step kernel, and the population-storing LB of the
 same library on the same box and GPU beside it.
 

@@ -11,9 +11,9 @@ Every function follows a passage of the paper (Tiribocchi et al.,
 and equation:
 
 * ``lattice``      -- D3Q19 / D3Q27 tables, c_s^2 = 1/3 (Sec. II, III A).
-* ``lb``           -- reconstruction (Eq. oper, eq-part, neq-part), projection
-                      (Eq. HYD), collision (Eq. coll, coll2), pull streaming
-                      (Eq. stream); the moment-only stepper and the two
+* ``lb``           -- reconstruction (Eqs. (4)-(6)), projection
+                      (Eqs. (1)-(3)), collision (Eqs. (7), (8)), pull streaming
+                      (Eq. (9)); the moment-only stepper and the two
                       population-storing steppers it is compared with.
 * ``diagnostics``  -- mass / momentum sums, <rho>_{rho>0.5} (Sec. IV,
                       Fig. 2), the local relative error of Fig. 3.

@@ -1,7 +1,7 @@
 """Field diagnostics of the validation section, FP64 (test infrastructure only).
 
 * total mass per component and total momentum (conserved by BGK collision and
-  periodic streaming, Eqs. coll and stream);
+  periodic streaming, Eqs. (7) and (9));
 * the droplet density <rho>_{rho > 0.5}: the mean of rho over the nodes where
   rho > 0.5 (strict), Sec. IV, Figs. 2, 5, 7.  For two components the
   averaged field is the droplet component rho^1 (the colour maps of Figs. 1,

@@ -4,7 +4,7 @@ Test infrastructure only: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``; never by the library.
 
 State of the moment-only scheme ("LB without populations", Sec. II-III): per
-node the ten hydrodynamic fields of Eq. (HYD), in the canonical order
+node the ten hydrodynamic fields of Eqs. (1)-(3), in the canonical order
 
     m = (rho, j_x, j_y, j_z, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz),  j = rho u,
 
@@ -15,19 +15,19 @@ workloads it runs are periodic boxes).
 Three steppers are provided:
 
 * ``step_moment_only``  -- the paper's method.  Per step and per direction
-  i, the post-collision population of Eq. (coll2) is reconstructed, written
+  i, the post-collision population of Eq. (8) is reconstructed, written
   literally as
       h'_i = w_i rho (1 + c_i.u / cs^2 + Q_i:uu) + (1 - omega) w_i Q_i:(P - P^eq),
       Q_iab = (c_ia c_ib - cs^2 delta_ab) / (2 cs^4),   P^eq = cs^2 rho I + rho u u,
-  from the moments of every node, pull-streamed along c_i (Eq. (stream):
+  from the moments of every node, pull-streamed along c_i (Eq. (9):
   h_i(x, t+1) = h'_i[H(x - c_i, t)]) and summed into the new moments with
-  Eq. (HYD).  Populations exist only one direction at a time.
+  Eqs. (1)-(3).  Populations exist only one direction at a time.
 * ``step_regularized_population`` -- the same collision applied to stored
-  populations f (f is projected with Eq. (HYD), re-expanded with Eq. (coll2)
+  populations f (f is projected with Eqs. (1)-(3), re-expanded with Eq. (8)
   and streamed).  This is the population-storing scheme the moment-only
   method reproduces (Sec. II: the reconstruction keeps exactly the ten
   moments).
-* ``step_bgk_population`` -- plain BGK on stored populations, Eq. (coll)
+* ``step_bgk_population`` -- plain BGK on stored populations, Eq. (7)
   applied to f itself (ghost components kept): the "standard LB with
   populations" the paper compares against in Sec. IV.
 
@@ -62,7 +62,7 @@ def tensor_from_fields(p6: np.ndarray) -> list:
 
 
 def unpack(m: np.ndarray):
-    """(rho, u, P) from canonical moments; u = j / rho (Eq. HYD), P as 3x3 list."""
+    """(rho, u, P) from canonical moments; u = j / rho (Eqs. (1)-(3)), P as 3x3 list."""
     m = _check_moments(m)
     rho = m[0]
     u = m[1:4] / rho
@@ -73,7 +73,7 @@ def unpack(m: np.ndarray):
 def equilibrium_pressure(rho: np.ndarray, u: np.ndarray) -> list:
     """Second-order equilibrium momentum flux P^eq_ab = cs^2 rho delta_ab + rho u_a u_b.
 
-    This is the second moment of h^eq in Eq. (eq-part).
+    This is the second moment of h^eq in Eq. (5).
     """
     return [[CS2 * rho * (a == b) + rho * u[a] * u[b] for b in range(3)] for a in range(3)]
 
@@ -92,7 +92,7 @@ def equilibrium_moments(rho: np.ndarray, u: np.ndarray) -> np.ndarray:
 
 
 def hermite_q(c_i: np.ndarray) -> np.ndarray:
-    """Q_iab = (c_ia c_ib - cs^2 delta_ab) / (2 cs^4)   (Sec. II, after Eq. oper)."""
+    """Q_iab = (c_ia c_ib - cs^2 delta_ab) / (2 cs^4)   (Sec. II, after Eq. (4))."""
     c = c_i.astype(np.float64)
     return (np.outer(c, c) - CS2 * np.eye(3)) / (2.0 * CS2 * CS2)
 
@@ -121,9 +121,9 @@ def reconstruct_direction(m, lat: Lattice, i: int, omega: float | None) -> np.nd
     """Population h_i at every node, reconstructed from the moments.
 
     ``m`` is a canonical moment array or a ``LocalFields`` built from one.
-    omega=None: Eq. (oper), h_i = h_i^eq + h_i^neq (Eqs. eq-part, neq-part),
+    omega=None: Eq. (4), h_i = h_i^eq + h_i^neq (Eqs. (5), (6)),
     ghosts g_i = 0.
-    omega given: the post-collision population of Eq. (coll2),
+    omega given: the post-collision population of Eq. (8),
     h'_i = h_i^eq + (1 - omega) h_i^neq.
     """
     fl = m if isinstance(m, LocalFields) else LocalFields(m)
@@ -133,21 +133,21 @@ def reconstruct_direction(m, lat: Lattice, i: int, omega: float | None) -> np.nd
     q = hermite_q(c)
     cu = (c[0] * u[0] + c[1] * u[1] + c[2] * u[2]) / CS2          # c_ia u_ia, u_ia = u_a / cs^2
     quu = _contract(q, fl.uu)
-    h_eq = w * rho * (1.0 + cu + quu)                              # Eq. (eq-part)
-    h_neq = w * _contract(q, fl.pneq)                              # Eq. (neq-part)
+    h_eq = w * rho * (1.0 + cu + quu)                              # Eq. (5)
+    h_neq = w * _contract(q, fl.pneq)                              # Eq. (6)
     if omega is None:
-        return h_eq + h_neq                                        # Eq. (oper)
-    return h_eq + (1.0 - omega) * h_neq                            # Eq. (coll2)
+        return h_eq + h_neq                                        # Eq. (4)
+    return h_eq + (1.0 - omega) * h_neq                            # Eq. (8)
 
 
 def reconstruct(m: np.ndarray, lat: Lattice, omega: float | None = None) -> np.ndarray:
-    """All Q reconstructed populations, shape (Q, nz, ny, nx) (Eq. oper / coll2)."""
+    """All Q reconstructed populations, shape (Q, nz, ny, nx) (Eq. (4) / (8))."""
     fl = LocalFields(m)
     return np.stack([reconstruct_direction(fl, lat, i, omega) for i in range(lat.Q)])
 
 
 def project(f: np.ndarray, lat: Lattice) -> np.ndarray:
-    """H = P f: the ten moments of a population set, Eq. (HYD)."""
+    """H = P f: the ten moments of a population set, Eqs. (1)-(3)."""
     f = np.asarray(f, dtype=np.float64)
     m = np.zeros((NFIELDS,) + f.shape[1:], dtype=np.float64)
     for i in range(lat.Q):
@@ -173,9 +173,9 @@ def stream_pull(field: np.ndarray, c_i: np.ndarray) -> np.ndarray:
 def step_moment_only(m: np.ndarray, lat: Lattice, tau: float) -> np.ndarray:
     """One time step of the moment-only scheme (reconstruct, collide, pull-stream, project).
 
-    Per direction: h'_i from Eq. (coll2) at every source node, streamed with
-    Eq. (stream) (no sum over i: the sum belongs to Eq. (HYD)), then added
-    into the new moments with Eq. (HYD).  Returns the new canonical moments.
+    Per direction: h'_i from Eq. (8) at every source node, streamed with
+    Eq. (9) (no sum over i: the sum belongs to Eqs. (1)-(3)), then added
+    into the new moments with Eqs. (1)-(3).  Returns the new canonical moments.
     """
     m = _check_moments(m)
     omega = 1.0 / tau
@@ -201,19 +201,19 @@ def run_moment_only(m: np.ndarray, lat: Lattice, tau: float, nsteps: int) -> np.
 
 
 def populations_from_moments(m: np.ndarray, lat: Lattice) -> np.ndarray:
-    """Initial populations f = R H for the population-storing schemes (Eq. oper)."""
+    """Initial populations f = R H for the population-storing schemes (Eq. (4))."""
     return reconstruct(_check_moments(m), lat, omega=None)
 
 
 def step_regularized_population(f: np.ndarray, lat: Lattice, tau: float) -> np.ndarray:
-    """Population-storing regularized step: f -> H = P f -> h' (Eq. coll2) -> stream."""
+    """Population-storing regularized step: f -> H = P f -> h' (Eq. (8)) -> stream."""
     fl = LocalFields(project(f, lat))
     omega = 1.0 / tau
     return np.stack([stream_pull(reconstruct_direction(fl, lat, i, omega), lat.c[i]) for i in range(lat.Q)])
 
 
 def step_bgk_population(f: np.ndarray, lat: Lattice, tau: float) -> np.ndarray:
-    """Standard BGK with stored populations: f' = (1 - omega) f + omega f^eq (Eq. coll on f), stream."""
+    """Standard BGK with stored populations: f' = (1 - omega) f + omega f^eq (Eq. (7) on f), stream."""
     fl = LocalFields(project(f, lat))
     rho, u = fl.rho, fl.u
     omega = 1.0 / tau
@@ -223,7 +223,7 @@ def step_bgk_population(f: np.ndarray, lat: Lattice, tau: float) -> np.ndarray:
         q = hermite_q(c)
         cu = (c[0] * u[0] + c[1] * u[1] + c[2] * u[2]) / CS2
         quu = _contract(q, fl.uu)
-        feq = lat.w[i] * rho * (1.0 + cu + quu)                    # Eq. (eq-part)
+        feq = lat.w[i] * rho * (1.0 + cu + quu)                    # Eq. (5)
         out[i] = stream_pull((1.0 - omega) * f[i] + omega * feq, c)
     return out
 
@@ -239,7 +239,7 @@ def node_moment_only(m: np.ndarray, lat: Lattice, tau: float, x: int, y: int, z:
     """New moments of ONE node after one moment-only step (pure-Python per-node form).
 
     Used to check sampled outputs of full-size GPU runs: it reads only the Q
-    source nodes x - c_i (periodic) and applies Eq. (coll2) / (stream) / (HYD)
+    source nodes x - c_i (periodic) and applies Eq. (8) / (9) / (1)-(3)
     to each, so it costs O(Q) regardless of the grid size.
     """
     m = _check_moments(m)

@@ -24,11 +24,11 @@ repository's design notes, one per step:
    far-field tails of the tanh profile, where |G| is tiny, out of the
    detector; the rise margin keeps exact ties (symmetric configurations)
    from being decided by rounding.
-3. collision of the reconstructed populations h (Eq. oper) by BGK (Eq. coll)
+3. collision of the reconstructed populations h (Eq. (4)) by BGK (Eq. (7))
    with a Guo forcing term, u_F = (j + F/2) / rho:
        h'_i = (1 - omega) h_i + omega h_i^eq(rho, u_F) + (1 - omega/2) S_i,
        S_i = w_i [(c_i - u_F)/cs^2 + (c_i.u_F) c_i / cs^4] . F
-   (for F = 0 this is Eq. coll2), plus the colour-gradient perturbation
+   (for F = 0 this is Eq. (8)), plus the colour-gradient perturbation
        Delta_i = (A_s / 2) |G| [w_i (c_i.n)^2 - w_i cs^2]
    applied to these populations (Sec. III A, last sentence) where the normal
    is defined (|G| >= g_min); elsewhere Delta_i = 0 (with n = 0 the bracket
@@ -40,7 +40,7 @@ repository's design notes, one per step:
 4. recolouring of the collided populations (Sec. III A):
        h1'_i = (rho1/rho) h'_i + beta (rho1 rho2 / rho) w_i (c_i.n) / |c_i|   (0 for c_i = 0),
        h2'_i = h'_i - h1'_i.
-5. pull streaming of both colours (Eq. stream) and projection (Eq. HYD):
+5. pull streaming of both colours (Eq. (9)) and projection (Eqs. (1)-(3)):
        rho1(x, t+1) = sum_i h1'_i(x - c_i), and rho, j, P from h' = h1' + h2'.
 
 ``step_moment_only`` keeps only the 11 fields (populations exist one
@@ -170,11 +170,11 @@ def collided_direction(cf: CollisionFields, lat: Lattice, i: int):
     w = lat.w[i]
     om = cf.omega
     rho = cf.rho
-    h = lb.reconstruct_direction(cf.fl, lat, i, None)                     # Eq. (oper)
+    h = lb.reconstruct_direction(cf.fl, lat, i, None)                     # Eq. (4)
     u = cf.uF
     cu = (c[0] * u[0] + c[1] * u[1] + c[2] * u[2]) / CS2
     usq = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
-    heq = w * rho * (1.0 + cu + 0.5 * cu * cu - 0.5 * usq / CS2)         # Eq. (eq-part) at u_F
+    heq = w * rho * (1.0 + cu + 0.5 * cu * cu - 0.5 * usq / CS2)         # Eq. (5) at u_F
     F = cf.F
     cF = c[0] * F[0] + c[1] * F[1] + c[2] * F[2]
     uFdot = u[0] * F[0] + u[1] * F[1] + u[2] * F[2]
@@ -187,7 +187,7 @@ def collided_direction(cf: CollisionFields, lat: Lattice, i: int):
         pert = 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2 * nn)
     else:
         pert = np.where(cf.iface, 0.5 * cf.prm.A_s * cf.gnorm * (w * cn * cn - w * CS2), 0.0)
-    hp = (1.0 - om) * h + om * heq + (1.0 - 0.5 * om) * S + pert          # Eq. (coll) + forcing + perturbation
+    hp = (1.0 - om) * h + om * heq + (1.0 - 0.5 * om) * S + pert          # Eq. (7) + forcing + perturbation
     cnorm = np.sqrt((c * c).sum())
     recol = 0.0 if cnorm == 0 else cf.prm.beta * (cf.rho1 * cf.rho2 / rho) * w * cn / cnorm
     h1 = (cf.rho1 / rho) * hp + recol
@@ -226,7 +226,7 @@ def run_moment_only(m, lat, tau, prm, nsteps):
 
 def populations_from_moments(m: np.ndarray, lat: Lattice) -> np.ndarray:
     """Colour population sets (f1, f2), shape (2, Q, ...), from 11-field moments:
-    f = R(total moments) (Eq. oper), split by the colour fractions."""
+    f = R(total moments) (Eq. (4)), split by the colour fractions."""
     m = _check(m)
     f = lb.populations_from_moments(total_moments(m), lat)
     rho = m[0] + m[1]

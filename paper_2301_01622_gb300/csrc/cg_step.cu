@@ -15,8 +15,8 @@
 //     A' = (1 - w) A + w rho u_F u_F + (1 - w/2)(u_F F + F u_F) + A_s cs^4 |G| n n
 //   post-collision populations g'_i = w_i [d + 3 c_i.j' + 4.5 c_i c_i:A' - 1.5 tr A']
 //   recolouring: h1'_i = (rho1/rho)(w_i + g'_i) + beta (rho1 rho2 / rho) w_i (c_i.n)/|c_i|
-// and per output node x: the total moments from sum_i g'_i(x - c_i) (Eq. stream,
-// HYD) and rho1(x) = sum_i h1'_i(x - c_i).
+// and per output node x: the total moments from sum_i g'_i(x - c_i) (Eqs. (9) and
+// (1)-(3)) and rho1(x) = sum_i h1'_i(x - c_i).
 //
 // The CTA marches a BX x BY column through z like the one-component tiled
 // kernel.  phi of the tile plus a two-node halo is kept for three planes

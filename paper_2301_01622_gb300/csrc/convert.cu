@@ -3,7 +3,7 @@
 //
 // canonical (one component): rho, j_x, j_y, j_z, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz
 // shifted storage:           d = rho - 1, j, A = P - cs^2 rho I
-// Equilibrium (second moment of Eq. eq-part): P^eq = cs^2 rho I + rho u u, so
+// Equilibrium (second moment of Eq. (5)): P^eq = cs^2 rho I + rho u u, so
 // A^eq = rho u u.  All conversions compute in FP64 and round once.
 // Two components: canonical rho1, rho2, j, P; state rho1, d = rho1 + rho2 - 1,
 // j, A (rho1 needs no shift: it lies in [0, rho]).

@@ -13,11 +13,11 @@
 // (1, 0, cs^2 I), the constant w_i part never has to be added into the
 // sums, which keeps FP32 rounding relative to the flow's deviations from rest.
 //
-// With A' the post-collision value of A, Eq. (coll2) reduces to
+// With A' the post-collision value of A, Eq. (8) reduces to
 //   h'_i = w_i [rho + 3 c_i.j + 4.5 c_i c_i : A' - 1.5 tr A'],
 //   A' = (1 - omega) A + omega j j / rho,
-// because P^eq = cs^2 rho I + rho u u makes the u u terms of Eq. (eq-part)
-// and Eq. (neq-part) cancel.  rho and j are unchanged by the collision.
+// because P^eq = cs^2 rho I + rho u u makes the u u terms of Eq. (5)
+// and Eq. (6) cancel.  rho and j are unchanged by the collision.
 #pragma once
 
 #include <cstdint>
@@ -127,7 +127,7 @@ struct Acc {
         if (cx * cz > 0) sxz += g; else if (cx * cz < 0) sxz -= g;
         if (cy * cz > 0) syz += g; else if (cy * cz < 0) syz -= g;
     }
-    // New shifted moments: A = S - cs^2 d I (Eq. HYD on h = w + g).
+    // New shifted moments: A = S - cs^2 d I (Eqs. (1)-(3) on h = w + g).
     __device__ __forceinline__ Mom<T> finish() const {
         Mom<T> m;
         const T t = T(kCs2) * d;

@@ -3,9 +3,9 @@
 // One step maps the shifted moments m(t) to m(t+1):
 //   1. collision at every source node y (local):  A'(y) = (1-omega) A + omega j j / rho
 //   2. reconstruction of the post-collision population travelling from y
-//      along c_i (Eq. coll2):  g'_i(y) = w_i [d + 3 c_i.j + 4.5 c_i c_i:A' - 1.5 tr A']
-//   3. pull streaming (Eq. stream):  g_i(x, t+1) = g'_i(x - c_i)
-//   4. projection (Eq. HYD):  d = sum g_i, j = sum g_i c_i, A = sum g_i c_i c_i - cs^2 d I
+//      along c_i (Eq. (8)):  g'_i(y) = w_i [d + 3 c_i.j + 4.5 c_i c_i:A' - 1.5 tr A']
+//   3. pull streaming (Eq. (9)):  g_i(x, t+1) = g'_i(x - c_i)
+//   4. projection (Eqs. (1)-(3)):  d = sum g_i, j = sum g_i c_i, A = sum g_i c_i c_i - cs^2 d I
 // No population is ever stored in global memory (Sec. III A, "without arrays").
 //
 // Three kernels:
@@ -186,7 +186,7 @@ __host__ __device__ constexpr bool wanted(int cx, int cy) {
 
 // Publish the crossing populations of one collided node into G[k][n].
 // Directions come in opposite pairs (c, -c) sharing the even part of Eq.
-// (coll2): g'_{+-c} = w (q +- l) with q = d - 1.5 tr A' + 4.5 c c : A',
+// (8): g'_{+-c} = w (q +- l) with q = d - 1.5 tr A' + 4.5 c c : A',
 // l = 3 c.j.
 template <class L, class T, int HN, int RX = kAny, int RY = kAny>
 __device__ __forceinline__ void publish(T* __restrict__ G, int n, const Mom<T>& c) {

@@ -2,13 +2,13 @@
 //
 // These keep all Q populations per node in global memory, the layout the
 // paper compares the moment-only method against (Sec. III A: 38 arrays for
-// D3Q19 in the flip-flop scheme; Sec. III C: the "standard" LB with
+// D3Q19 in the flip-flop scheme; Sec. IV A: the "standard" LB with
 // populations).  Each kernel is the usual one-thread-per-node pull step:
 // read f_i(x - c_i) (post-collision values of the previous step), project
-// to moments (Eq. HYD), collide, write the Q post-collision values at x.
-//   regularized: f'_i = h^eq_i + (1 - omega) h^neq_i from the moments (Eq. coll2),
+// to moments (Eqs. (1)-(3)), collide, write the Q post-collision values at x.
+//   regularized: f'_i = h^eq_i + (1 - omega) h^neq_i from the moments (Eq. (8)),
 //                the same map as the moment-only step;
-//   BGK:         f'_i = (1 - omega) f_i + omega h^eq_i (Eq. coll on the stored f_i),
+//   BGK:         f'_i = (1 - omega) f_i + omega h^eq_i (Eq. (7) on the stored f_i),
 //                which keeps the ghost components.
 // The state holds shifted values g_i = f_i - w_i in a dense [Q][N] layout;
 // direction k runs over (cz, cy, cx) in {-1,0,1}^3 in that loop order,

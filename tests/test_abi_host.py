@@ -55,7 +55,7 @@ def test_storage_accounting_matches_paper():
     assert mom2.arrays == g["hydro_arrays_two_component_flipflop"]["value"]
     assert pop2.arrays == g["population_arrays_d3q19_two_component_flipflop"]["value"]
     # the streaming step of the two-component D3Q19 scheme reads 11 fields at
-    # 18 neighbours: 198 values, 792 bytes in FP32 (Sec. III C)
+    # 18 neighbours: 198 values, 792 bytes in FP32 (Sec. IV A)
     assert mom2.fields * 18 == g["stream_reads_two_component_d3q19"]["value"]
     assert mom2.fields * 18 * 4 == g["stream_read_bytes_fp32_two_component_d3q19"]["value"]
     # bytes per node and state size (FP32)

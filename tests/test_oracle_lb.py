@@ -6,7 +6,7 @@ one-step results, an exact Navier-Stokes decay rate (nu = cs^2 (tau - 1/2),
 Sec. III B), Galilean advection, a linear amplification matrix derived
 independently, conservation laws, and the population-storing form of the
 same scheme.  A dropped term, wrong sign, wrong index or transposed operand
-in the oracle's Eq. (oper)/(coll2)/(stream)/(HYD) fails at least one of them.
+in the oracle's Eq. (4)/(8)/(9)/(1)-(3) fails at least one of them.
 """
 import itertools
 import math
@@ -55,7 +55,7 @@ def test_reconstruction_reproduces_moments(lat):
 
 @pytest.mark.parametrize("lat", LATTICES, ids=IDS)
 def test_equilibrium_matches_textbook_expansion(lat):
-    """h^eq of Eq. (eq-part) equals the textbook second-order equilibrium
+    """h^eq of Eq. (5) equals the textbook second-order equilibrium
     w rho [1 + c.u/cs^2 + (c.u)^2/(2 cs^4) - u^2/(2 cs^2)], and its moments are
     (rho, rho u, cs^2 rho I + rho u u)."""
     rng = np.random.default_rng(3)
@@ -68,7 +68,7 @@ def test_equilibrium_matches_textbook_expansion(lat):
         cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2]
         usq = (u * u).sum(axis=0)
         textbook = lat.w[i] * rho * (1 + cu / CS2 + cu * cu / (2 * CS2 * CS2) - usq / (2 * CS2))
-        # P = P^eq: no non-equilibrium part, so Eq. (oper) is h^eq alone
+        # P = P^eq: no non-equilibrium part, so Eq. (4) is h^eq alone
         np.testing.assert_allclose(lb.reconstruct_direction(fl, lat, i, None), textbook, rtol=0, atol=1e-15)
     f = np.stack([lb.reconstruct_direction(fl, lat, i, None) for i in range(lat.Q)])
     mom = lb.project(f, lat)
@@ -81,7 +81,7 @@ def test_equilibrium_matches_textbook_expansion(lat):
 @pytest.mark.parametrize("lat", LATTICES, ids=IDS)
 @pytest.mark.parametrize("tau", [0.6, 1.0, 1.7])
 def test_coll2_literal_equals_moment_form(lat, tau):
-    """Eq. (coll2) written literally equals the linear moment form
+    """Eq. (8) written literally equals the linear moment form
     h'_i = w_i [rho + 3 c.j + 4.5 c c : A' - 1.5 tr A'],
     A' = (1 - omega)(P - cs^2 rho I) + omega j j / rho  (the u u terms cancel)."""
     m = inputs.random_moments(4, 3, 2, seed=11)
@@ -103,7 +103,7 @@ def test_coll2_literal_equals_moment_form(lat, tau):
 
 @pytest.mark.parametrize("lat", LATTICES, ids=IDS)
 def test_collided_moments_closed_form(lat):
-    """Moments of h' (Eq. coll2): rho and j unchanged, P' = P^eq + (1 - omega)(P - P^eq)."""
+    """Moments of h' (Eq. (8)): rho and j unchanged, P' = P^eq + (1 - omega)(P - P^eq)."""
     m = inputs.random_moments(3, 3, 3, seed=5)
     tau = 0.7
     omega = 1.0 / tau

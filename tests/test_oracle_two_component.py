@@ -260,3 +260,129 @@ def test_smooth_norm_conserves_colours_and_matches_populations(lat):
     mp = tc.project(f, lat)
     for k in range(11):
         assert np.abs(m[k] - mp[k]).max() <= 1e-12 * max(np.abs(mp[k]).max(), 1e-3)
+
+
+# Lattice sums K = sum_i w_i c_ix c_ix / |c_i| (the same for every axis; the
+# off-diagonal sums vanish), evaluated by hand shell by shell:
+#   D3Q19: 6 axis vectors, w = 1/18, sum c_x^2 = 2  -> 2/18
+#          12 edge vectors, w = 1/36, |c| = sqrt 2, sum c_x^2 = 8 -> 8/(36 sqrt 2)
+#   D3Q27: 6 axis, w = 2/27 -> 4/27; 12 edge, w = 1/54 -> 8/(54 sqrt 2);
+#          8 corners, w = 1/216, |c| = sqrt 3, sum c_x^2 = 8 -> 8/(216 sqrt 3)
+RECOLOUR_K = {
+    "D3Q19": 2.0 / 18.0 + 8.0 / (36.0 * math.sqrt(2.0)),
+    "D3Q27": 4.0 / 27.0 + 8.0 / (54.0 * math.sqrt(2.0)) + 8.0 / (216.0 * math.sqrt(3.0)),
+}
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_recolouring_first_moment_closed_form(lat):
+    """Recolouring (Sec. III A, Latva-Kokko reading): the colour-1 populations
+    differ from the colour-blind split (rho1/rho) h'_i only by
+    beta (rho1 rho2 / rho) w_i (c_i.n)/|c_i|, whose zeroth and second moments
+    vanish and whose first moment is beta (rho1 rho2 / rho) K n with the
+    hand-evaluated lattice sum K above.  Dropping the 1/|c_i| factor
+    (K = cs^2) or weighting by |c_i| instead fails this pin."""
+    m = inputs.random_moments(6, 5, 4, seed=17, nfields=11)
+    prm = tc.CGParams(beta=0.6, A_s=0.05, A_h=0.0)
+    cf = tc.CollisionFields(m, lat, 0.7, prm)
+    assert cf.iface.all()
+    hs = [tc.collided_direction(cf, lat, i) for i in range(lat.Q)]
+    hp = np.stack([h[0] for h in hs])
+    h1 = np.stack([h[1] for h in hs])
+    diff = h1 - (cf.rho1 / cf.rho) * hp
+    mom = lb.project(diff, lat)
+    e = prm.beta * cf.rho1 * cf.rho2 / cf.rho
+    K = RECOLOUR_K[lat.name]
+    assert abs(K - CS2) > 0.02
+    np.testing.assert_allclose(mom[0], 0.0, atol=1e-15)
+    for a in range(3):
+        np.testing.assert_allclose(mom[1 + a], e * K * cf.n[a], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(mom[4:], 0.0, atol=1e-15)
+    # the unit normal is unit where defined
+    np.testing.assert_allclose((cf.n ** 2).sum(axis=0), 1.0, atol=1e-14)
+
+
+def _ghosted_colour_populations(lat, shape, seed):
+    """Colour population sets with non-hydrodynamic (ghost) content: the
+    Hermite reconstruction of random moments plus a small random part, so
+    that BGK on the stored populations differs from the regularized step."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    m = inputs.random_moments(nx, ny, nz, seed=seed, nfields=11)
+    f12 = tc.populations_from_moments(m, lat)
+    f12 = f12 * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, size=f12.shape))
+    return f12
+
+
+def _textbook_feq(lat, rho, u):
+    """Second-order equilibrium w rho (1 + c.u/cs^2 + (c.u)^2/(2 cs^4) - u^2/(2 cs^2))."""
+    usq = u[0] ** 2 + u[1] ** 2 + u[2] ** 2
+    out = []
+    for i in range(lat.Q):
+        cu = sum(lat.c[i][a] * u[a] for a in range(3))
+        out.append(lat.w[i] * rho * (1 + cu / CS2 + cu * cu / (2 * CS2 * CS2) - usq / (2 * CS2)))
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_bgk_population_passive_colour_limit(lat):
+    """BGK with stored colour populations, beta = A_s = A_h = 0: the mixture
+    f = f1 + f2 follows the one-component BGK step (Eq. (7) on the stored
+    populations, ghosts kept), and colour 1 carries the fraction rho1/rho of
+    every post-collision population, f1'_i = (rho1/rho)[(1 - w) f_i + w f_i^eq],
+    streamed along c_i."""
+    f12 = _ghosted_colour_populations(lat, (6, 5, 4), seed=31)
+    tau = 0.7
+    om = 1.0 / tau
+    prm = tc.CGParams(beta=0.0, A_s=0.0, A_h=0.0)
+    out = tc.step_bgk_population(f12, lat, tau, prm)
+    f = f12[0] + f12[1]
+    np.testing.assert_allclose(out[0] + out[1], lb.step_bgk_population(f, lat, tau), rtol=0, atol=1e-15)
+    rho = f.sum(axis=0)
+    rho1 = f12[0].sum(axis=0)
+    u = np.stack([sum(lat.c[i][a] * f[i] for i in range(lat.Q)) for a in range(3)]) / rho
+    feq = _textbook_feq(lat, rho, u)
+    for i in range(lat.Q):
+        expect = lb.stream_pull((rho1 / rho) * ((1 - om) * f[i] + om * feq[i]), lat.c[i])
+        np.testing.assert_allclose(out[0, i], expect, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+def test_bgk_population_equals_regularized_at_tau_one(lat):
+    """At tau = 1 (omega = 1) the BGK step forgets the stored non-equilibrium
+    part, so BGK-2 and the regularized colour-population step are the same map,
+    recolouring, perturbation and near-contact force included."""
+    r1, r2, u = _pair((24, 14, 14), radius=3.5, gap=2.5, speed=0.03, impact=1.0)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.01, h_c=3)
+    assert tc.CollisionFields(_moments(r1, r2, u), lat, 1.0, prm).near.any()
+    f0 = tc.populations_from_moments(_moments(r1, r2, u), lat)
+    rng = np.random.default_rng(4)
+    f0 = f0 * (1.0 + 0.02 * rng.uniform(-1.0, 1.0, size=f0.shape))
+    fb = tc.run_population(f0, lat, 1.0, prm, 5, scheme="bgk")
+    fr = tc.run_population(f0, lat, 1.0, prm, 5, scheme="regularized")
+    np.testing.assert_allclose(fb, fr, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("lat", LATTICES, ids=IDS)
+@pytest.mark.parametrize("A_h", [0.0, 0.02])
+def test_bgk_population_conservation(lat, A_h):
+    """BGK-2 away from tau = 1, with ghosts, recolouring and perturbation:
+    each colour's mass is conserved and the total momentum changes by exactly
+    the sum of the near-contact force each step (zero for A_h = 0)."""
+    r1, r2, u = _pair((24, 14, 14), radius=3.5, gap=2.0, speed=0.03, impact=2.0)
+    f = tc.populations_from_moments(_moments(r1, r2, u), lat)
+    rng = np.random.default_rng(8)
+    f = f * (1.0 + 0.02 * rng.uniform(-1.0, 1.0, size=f.shape))
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=A_h, h_c=3)
+    tau = 0.7
+    mass0 = [math.fsum(f[k].ravel()) for k in range(2)]
+    for _ in range(5):
+        m = tc.project(f, lat)
+        cf = tc.CollisionFields(m, lat, tau, prm)
+        jF = [math.fsum(m[2 + a].ravel()) + math.fsum(cf.F[a].ravel()) for a in range(3)]
+        f = tc.step_bgk_population(f, lat, tau, prm)
+        m = tc.project(f, lat)
+        for a in range(3):
+            assert abs(math.fsum(m[2 + a].ravel()) - jF[a]) < 1e-13
+    for k in range(2):
+        assert abs(math.fsum(f[k].ravel()) - mass0[k]) < 1e-11
