@@ -36,6 +36,9 @@ LATTICE = 19
 TAU = 0.6
 U0, NOISE, SEED = 0.05, 1e-3, 2301
 WORKLOAD = "256^3 periodic D3Q19 moment-only LB, FP32, Taylor-Green u0=0.05 + U(-1e-3,1e-3) noise, tau=0.6"
+# near-contact strength of the bench's droplet collision: the paper's value, with which the
+# 20000-step run of the 384 x 192 x 192 pair ends as two droplets (A_h = 0: one)
+OUTCOME_A_H = 0.01
 L2_NOTE = "inputs larger than L2 (each FP32 state copy 671 MB vs 129 MB L2); no flush"
 
 
@@ -50,7 +53,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the D3Q27 and population lines")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tma", "tiled", "direct"],
                     help="moment-only kernel (auto = the library's choice)")
-    ap.add_argument("--variant", type=int, default=0, help="kernel variant (tuning; tiled 0..9, TMA 0..4)")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant (tuning; tiled 0..5, TMA 0..2)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="lattice of the main line")
     ap.add_argument("--cg-variant", type=int, default=0, help="two-component kernel variant (tuning)")
     ap.add_argument("--ref-budget", type=float, default=150.0,
@@ -236,14 +239,14 @@ def gpu_arm(args, rank, world, local):
     nodes = NX * NY * NZ
     peak, peak_src = measured_peaks()
 
-    def run(lattice, scheme, sampler=None):
-        ctx = make_ctx(llb, lattice, scheme, stream)
+    def run(lattice, scheme, sampler=None, storage=None):
+        ctx = make_ctx(llb, lattice, scheme, stream, storage=storage)
         try:
             llb.llb_init_equilibrium(ctx, rho, u)
             kernel = llb.llb_state_device(ctx)[2]
             ms, clocks = time_steps(llb, ctx, args.steps, args.warmup, world, sampler)
-            fp = llb.llb_footprint_query(NX, NY, NZ, lattice,
-                                         llb.llb_params_default(scheme=scheme))
+            fp = llb.llb_footprint_query(NX, NY, NZ, lattice, llb.llb_params_default(
+                scheme=scheme, storage=llb.LLB_F32 if storage is None else storage))
         finally:
             llb.llb_destroy(ctx)
         ms_max = reduce_max(ms, world)
@@ -260,9 +263,14 @@ def gpu_arm(args, rank, world, local):
         extra["population_d3q19"] = run(19, llb.LLB_SCHEME_POPULATION)
         extra["moment_d3q27"] = run(27, llb.LLB_SCHEME_MOMENT)
         extra["population_d3q27"] = run(27, llb.LLB_SCHEME_POPULATION)
+        # 16-bit shifted/scaled storage, FP32 arithmetic (40 B/node)
+        for q in (19, 27):
+            extra[f"moment_d3q{q}_fp16"] = run(q, llb.LLB_SCHEME_MOMENT, storage=llb.LLB_F16S)
+            extra[f"moment_d3q{q}_bf16"] = run(q, llb.LLB_SCHEME_MOMENT, storage=llb.LLB_BF16S)
 
     if not args.no_extra:
-        extra["two_component_d3q27"] = droplet_arm(args, llb, inputs, stream, world, peak)
+        extra["two_component_d3q27"] = droplet_arm(args, llb, inputs, stream, world, peak, OUTCOME_A_H,
+                                                   "near-contact force on: the pair does not merge")
         extra["batched_ensemble"] = ensemble_arm(args, llb, inputs, stream, world, peak)
         extra["adjoint_two_component_d3q27"] = adjoint_arm(args, llb, inputs, stream, world)
 
@@ -284,29 +292,39 @@ def gpu_arm(args, rank, world, local):
     return main, extra, e2e, {"ms": diag_ms, "mass": diag["mass"][0], "flags": diag["flags"]}, peak, peak_src
 
 
-def droplet_arm(args, llb, inputs, stream, world, peak):
+def droplet_arm(args, llb, inputs, stream, world, peak, A_h, label):
     """Two-component D3Q27 droplet collision, 384 x 192 x 192, FP32, tau = 1,
-    R = 30, +-0.05 along x, impact parameter 0.5 R, near-contact force on
-    (A_h = 0.01): MLUPS of the fused colour-gradient step (88 B/node)."""
-    import torch
+    R = 30, +-0.05 along x, impact parameter 0.5 R: MLUPS of the fused
+    moment-only colour-gradient step (88 B/node), and of the colour-gradient
+    LB with stored colour populations on the same field (BGK collision, the
+    paper's "standard CGLB"; 432 B/node algorithmic: 2Q populations read and
+    written; the implementation is the split approach, a phase-field pass and
+    a collide-and-stream pass, which moves ~656 B/node)."""
     nx, ny, nz = 384, 192, 192
     r1, r2, u = inputs.droplet_pair(nx, ny, nz, 30.0, 0.05, 15.0)
-    p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F32, A_h=0.01, A_s=0.01, beta=0.7, stream=stream,
-                               variant=getattr(args, "cg_variant", 0))
-    ctx = llb.llb_create(nx, ny, nz, 27, 1.0, p)
-    try:
-        llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
-        steps = max(10, args.steps // 4)
-        ms, _ = time_steps(llb, ctx, steps, max(3, args.warmup), world)
-    finally:
-        llb.llb_destroy(ctx)
-    ms = reduce_max(ms, world)
     nodes = nx * ny * nz
-    t = ms / 1e3 / steps
-    gbs = 88 * nodes / t / 1e9
-    return {"mlups": world * nodes / t / 1e6, "frac": gbs / peak, "achieved_gbs": gbs, "bytes_per_node": 88,
-            "ms_per_step": ms / steps, "steps": steps,
-            "workload": "384x192x192 D3Q27 two-component CG + near-contact, FP32, tau=1, R=30, U=+-0.05, b=0.5R"}
+    steps = max(10, args.steps // 4)
+    out = {}
+    for key, scheme, bpn in (("moment", llb.LLB_SCHEME_MOMENT, 88),
+                             ("population_bgk", llb.LLB_SCHEME_POPULATION_BGK, 2 * 2 * 27 * 4)):
+        p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F32, A_h=A_h, A_s=0.01, beta=0.7, stream=stream,
+                                   scheme=scheme, variant=getattr(args, "cg_variant", 0) if key == "moment" else 0)
+        ctx = llb.llb_create(nx, ny, nz, 27, 1.0, p)
+        try:
+            llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
+            ms, _ = time_steps(llb, ctx, steps, max(3, args.warmup), world)
+        finally:
+            llb.llb_destroy(ctx)
+        ms = reduce_max(ms, world)
+        t = ms / 1e3 / steps
+        gbs = bpn * nodes / t / 1e9
+        out[key] = {"mlups": world * nodes / t / 1e6, "frac": gbs / peak, "achieved_gbs": gbs, "bytes_per_node": bpn,
+                    "ms_per_step": ms / steps, "steps": steps}
+    line = dict(out["moment"])
+    line["workload"] = f"384x192x192 D3Q27 two-component CG, FP32, tau=1, R=30, U=+-0.05, b=0.5R, A_h={A_h} ({label})"
+    line["population_bgk"] = out["population_bgk"]
+    line["speedup_vs_population"] = out["moment"]["mlups"] / out["population_bgk"]["mlups"]
+    return line
 
 
 def ensemble_arm(args, llb, inputs, stream, world, peak):
@@ -380,7 +398,10 @@ def adjoint_arm(args, llb, inputs, stream, world):
 
 
 def e2e_arm(args, llb, rho, u, stream, world):
-    """Per step: pinned host canonical FP32 moments -> device, one step, device -> pinned host."""
+    """Per step, through the public C ABI: pinned host canonical FP32 moments ->
+    device, one step, device -> pinned host (llb_step_host, which overlaps the
+    slab copies with the per-slab steps); the sequential form
+    (llb_init_moments + llb_step + llb_get_moments) is timed beside it."""
     import torch
 
     nodes = NX * NY * NZ
@@ -394,24 +415,33 @@ def e2e_arm(args, llb, rho, u, stream, world):
         h_in.copy_(dev)
         torch.cuda.synchronize()
         k = max(1, args.e2e_steps)
-        for _ in range(2):
-            llb.llb_init_moments(ctx, h_in)
-            llb.llb_step(ctx, 1)
-            llb.llb_get_moments(ctx, h_out)
-        barrier(world)
-        t0 = time.perf_counter()
-        for _ in range(k):
-            llb.llb_init_moments(ctx, h_in)
-            llb.llb_step(ctx, 1)
-            llb.llb_get_moments(ctx, h_out)
-        torch.cuda.synchronize()
-        dt = reduce_max(time.perf_counter() - t0, world)
+        times = {}
+        for name in ("sequential", "overlapped"):
+            def one():
+                if name == "overlapped":
+                    llb.llb_step_host(ctx, h_in, h_out, 1)
+                else:
+                    llb.llb_init_moments(ctx, h_in)
+                    llb.llb_step(ctx, 1)
+                    llb.llb_get_moments(ctx, h_out)
+            for _ in range(2):
+                one()
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(k):
+                one()
+            torch.cuda.synchronize()
+            times[name] = reduce_max(time.perf_counter() - t0, world)
     finally:
         llb.llb_destroy(ctx)
     nbytes = 10 * nodes * 4
+    dt = times["overlapped"]
     return {"value": world * nodes * k / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "steps": k,
-            "path": "llb_init_moments(host) + llb_step(1) + llb_get_moments(host), FP32 canonical, pinned"}
+            "path": "llb_step_host(host in, 1 step, host out), FP32 canonical, pinned, copies overlapped with "
+                    "per-slab steps",
+            "sequential_mlups": world * nodes * k / times["sequential"] / 1e6,
+            "sequential_path": "llb_init_moments(host) + llb_step(1) + llb_get_moments(host)"}
 
 
 # ----------------------------------------------------------------------------- CPU (oracle) legs
@@ -424,9 +454,37 @@ def oracle_sample(nz_sample):
     return rho[:nz_sample].copy(), u[:, :nz_sample].copy()
 
 
+def _slab_step(args):
+    """One oracle step of a z-slab with one halo plane on each side (runs in a
+    worker process); returns the interior planes and the step's wall time."""
+    from oracle import D3Q19, lb
+    slab, tau = args
+    t0 = time.perf_counter()
+    new = lb.step_moment_only(slab, D3Q19, tau)
+    return new[:, 1:-1], time.perf_counter() - t0
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(gpu_check: bool):
-    """Time the FP64 oracle on one full-size step (the bench field), and use its
-    result to check the GPU's first step at FP32 tolerance."""
+    """Time the FP64 oracle on one full-size step of the bench field, on one
+    host core and on all host cores (the field split into z-slabs with one
+    halo plane each, one oracle step per slab in parallel worker processes;
+    time = the slowest worker's step, data distribution excluded), and use its
+    result to check the GPU's first step per shifted field at FP32 and
+    16-bit storage."""
+    import multiprocessing as mp
+
     from oracle import D3Q19, lb
     from paper_2301_01622_gb300 import inputs, llb
 
@@ -435,25 +493,68 @@ def cpu_baseline(gpu_check: bool):
     t0 = time.perf_counter()
     ref = lb.step_moment_only(m0, D3Q19, TAU)
     dt = time.perf_counter() - t0
-    out = {"value": NX * NY * NZ / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-           "sample": "one time step of the full 256^3 D3Q19 workload, numpy FP64, single thread",
-           "seconds": dt}
+    nodes = NX * NY * NZ
+    cores = max(1, min(os.cpu_count() or 1, 32))
+    par = None
+    if cores > 1:
+        bounds = [(k * NZ) // cores for k in range(cores + 1)]
+        slabs = [np.take(m0, range(bounds[k] - 1, bounds[k + 1] + 1), axis=1, mode="wrap") for k in range(cores)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_slab_step, [(sl, TAU) for sl in slabs])
+        got_par = np.concatenate([r[0] for r in res], axis=1)
+        par_dt = max(r[1] for r in res)
+        par = {"value": nodes / par_dt / 1e6, "unit": "MLUPS", "cores": cores, "seconds": par_dt,
+               "matches_single_core": bool(np.array_equal(got_par, ref))}
+    single = {"value": nodes / dt / 1e6, "unit": "MLUPS", "cores": 1, "seconds": dt}
+    if par is not None:
+        out = {"value": par["value"], "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"one time step of the full 256^3 D3Q19 workload, numpy FP64, split into {cores} z-slabs "
+                         "(one halo plane each) stepped in parallel worker processes",
+               "seconds": par["seconds"], "matches_single_core": par["matches_single_core"],
+               "single_core": single, "cpu_model": _cpu_model()}
+    else:
+        out = {"value": single["value"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "one time step of the full 256^3 D3Q19 workload, numpy FP64, single thread",
+               "seconds": dt, "cpu_model": _cpu_model()}
     parity = None
     if gpu_check:
         import torch
-        ctx = make_ctx(llb, LATTICE, llb.LLB_SCHEME_MOMENT, torch.cuda.current_stream().cuda_stream)
-        try:
-            llb.llb_init_equilibrium(ctx, rho, u)
-            llb.llb_step(ctx, 1)
-            got = llb.llb_get_moments(ctx, np.empty((10, NZ, NY, NX)))
-        finally:
-            llb.llb_destroy(ctx)
-        errs = {}
-        for name, sl in (("rho", slice(0, 1)), ("j", slice(1, 4)), ("P", slice(4, 10))):
-            errs[name] = float(np.abs(got[sl] - ref[sl]).max() / np.abs(ref[sl]).max())
-        parity = {"max_rel_err": errs, "tol": 1e-5, "pass": all(v <= 1e-5 for v in errs.values()),
-                  "vs": "FP64 oracle, one step of the full 256^3 field"}
+        parity = {"vs": "FP64 oracle, one step of the full 256^3 field, per shifted field "
+                        "(max |gpu - oracle| / max |oracle| of rho-1, each j, each A = P - cs^2 rho I)"}
+        for name, storage, tol in (("fp32", llb.LLB_F32, 1e-5), ("fp16", llb.LLB_F16S, None),
+                                   ("bf16", llb.LLB_BF16S, None)):
+            ctx = make_ctx(llb, LATTICE, llb.LLB_SCHEME_MOMENT, torch.cuda.current_stream().cuda_stream,
+                           storage=storage)
+            try:
+                llb.llb_init_equilibrium(ctx, rho, u)
+                llb.llb_step(ctx, 1)
+                got = llb.llb_get_moments(ctx, np.empty((10, NZ, NY, NX)))
+            finally:
+                llb.llb_destroy(ctx)
+            errs = _field_errors(got, ref)
+            parity[name] = {"max_rel_err": errs, "max": max(errs.values())}
+            if tol is not None:
+                parity[name]["tol"] = tol
+                parity[name]["pass"] = all(v <= tol for v in errs.values())
     return out, parity
+
+
+def _field_errors(got, ref):
+    """Per shifted field: max |got - ref| / max |ref| (rho - 1, j, A = P - cs^2 rho I)."""
+    cs2 = 1.0 / 3.0
+    names = ["drho", "jx", "jy", "jz", "Axx", "Ayy", "Azz", "Axy", "Axz", "Ayz"]
+
+    def shifted(m):
+        sh = np.empty_like(m)
+        sh[0] = m[0] - 1.0
+        sh[1:4] = m[1:4]
+        sh[4:10] = m[4:10]
+        for a in range(3):
+            sh[4 + a] = m[4 + a] - cs2 * m[0]
+        return sh
+
+    g, r = shifted(got), shifted(ref)
+    return {nm: float(np.abs(g[k] - r[k]).max() / np.abs(r[k]).max()) for k, nm in enumerate(names)}
 
 
 def reference_arm(args, rank):
@@ -531,6 +632,10 @@ def main():
         "population_d3q19": _short(extra.get("population_d3q19")),
         "moment_d3q27": _short(extra.get("moment_d3q27")),
         "population_d3q27": _short(extra.get("population_d3q27")),
+        "moment_d3q19_fp16": _short(extra.get("moment_d3q19_fp16")),
+        "moment_d3q19_bf16": _short(extra.get("moment_d3q19_bf16")),
+        "moment_d3q27_fp16": _short(extra.get("moment_d3q27_fp16")),
+        "moment_d3q27_bf16": _short(extra.get("moment_d3q27_bf16")),
         "two_component_d3q27": extra.get("two_component_d3q27"),
         "batched_ensemble": extra.get("batched_ensemble"),
         "adjoint_two_component_d3q27": extra.get("adjoint_two_component_d3q27"),

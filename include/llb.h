@@ -6,11 +6,11 @@
  *
  * What one step computes (Sec. II and III A of the paper): every node holds
  * only its hydrodynamic moments -- density rho, momentum j = rho u and the
- * momentum-flux tensor P (Eq. HYD), ten fields for one component and eleven
+ * momentum-flux tensor P (Eqs. (1)-(3)), ten fields for one component and eleven
  * for two.  A step reconstructs each neighbour's post-collision population
- * from that neighbour's moments (Eq. oper, eq-part, neq-part, coll2),
- * pull-streams it (Eq. stream, read as h_i(x, t+1) = h'_i[H(x - c_i, t)]),
- * and sums the streamed populations into the new moments (Eq. HYD).  Two
+ * from that neighbour's moments (Eqs. (4)-(6) and (8)),
+ * pull-streams it (Eq. (9), read as h_i(x, t+1) = h'_i[H(x - c_i, t)]),
+ * and sums the streamed populations into the new moments (Eqs. (1)-(3)).  Two
  * flip-flop copies of the moment arrays hold times t and t+1 (Sec. III A).
  * Boundaries are periodic in x, y and z.
  *
@@ -74,12 +74,15 @@ extern "C" {
 /* ---- schemes --------------------------------------------------------- */
 /* The moment-only scheme of the paper (Sec. II-III A). */
 #define LLB_SCHEME_MOMENT          0
-/* Population-storing regularized LB: stores all Q populations and applies
- * the same collision (Eq. coll2 on the projected moments) -- the same map as
- * LLB_SCHEME_MOMENT in exact arithmetic, used as the in-project baseline.  */
+/* Population-storing regularized LB: stores all Q populations (2Q for two
+ * components: the total and colour-1 sets) and applies the same collision
+ * (Eq. (8) on the projected moments; for two components the same forcing,
+ * perturbation and recolouring) -- the same map as LLB_SCHEME_MOMENT in
+ * exact arithmetic, used as the in-project baseline.  FP32 or FP64.       */
 #define LLB_SCHEME_POPULATION      1
-/* Population-storing plain BGK (Eq. coll applied to the stored populations,
- * ghosts kept): the "standard LB with populations" of Sec. IV.            */
+/* Population-storing plain BGK (Eq. (7) applied to the stored populations,
+ * ghosts kept): the "standard LB with populations" of Sec. IV (for two
+ * components the colour-gradient LB with populations of Sec. IV A).      */
 #define LLB_SCHEME_POPULATION_BGK  2
 
 /* ---- kernel choice for LLB_SCHEME_MOMENT ----------------------------- */
@@ -95,14 +98,15 @@ typedef struct llb_params {
     int storage;      /* LLB_F32 (default), LLB_F64, LLB_F16S, LLB_BF16S     */
     int scheme;       /* LLB_SCHEME_* (default LLB_SCHEME_MOMENT)            */
     int kernel;       /* LLB_KERNEL_* (default LLB_KERNEL_AUTO)              */
-    int variant;      /* tuning variant, 0 = default: tiled kernel 0..9
-                         (tile shape, CTAs per SM, split-phase plane
-                         barrier, IEEE or approximate FP32 1/rho, dedicated
-                         halo warps), TMA
-                         kernel 0..4, two
-                         components 0..1; a variant the kernel does not have
-                         is LLB_EINVAL.  Every variant computes the same
-                         step (to FP32 rounding)                             */
+    int variant;      /* tuning variant, 0 = default.  One component, FP32:
+                         tiled kernel 0..5 (TMA L2 prefetch, IEEE 1/rho,
+                         64x8 and 32x8 tiles, split-phase plane barrier),
+                         TMA kernel 0..2 (ring depth, tile); the other
+                         storage types have one shape per kernel.  Two
+                         components 0..3 (tiles 32x8, 64x4, 32x8 with
+                         approximate FP32 quotients, 32x16).  A variant the
+                         kernel does not have is LLB_EINVAL.  Every variant
+                         computes the same step (to FP32 rounding)           */
     /* two-component colour-gradient / near-contact parameters (Sec. III A-B) */
     double beta;      /* recolouring strength, default 0.7                   */
     double A_s;       /* surface-tension (perturbation) strength, default 0.01 */
@@ -193,7 +197,7 @@ LLB_API int llb_init_moments(llb_ctx* ctx, const void* host_m, int host_dtype);
 LLB_API int llb_init_moments_device(llb_ctx* ctx, const void* dev_m, int dtype);
 
 /* Initialise at local equilibrium, P = cs^2 rho I + rho u u (the second
- * moment of Eq. eq-part), from HOST arrays: rho (ncomp fields: rho, or
+ * moment of Eq. (5)), from HOST arrays: rho (ncomp fields: rho, or
  * rho1 then rho2) and u (3 fields), canonical layout, element type
  * host_dtype. */
 LLB_API int llb_init_equilibrium(llb_ctx* ctx, const void* host_rho, const void* host_u, int host_dtype);
@@ -231,25 +235,46 @@ LLB_API int llb_diagnostics(llb_ctx* ctx, llb_diag* out);
  * llb_diagnostics, for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a deployment convenience.
  *
- * Who needs it: code that runs while a stream is being captured into a CUDA
- * graph (an allocation there invalidates the capture), frameworks that own
- * the device allocator, real-time loops that forbid allocation on the hot
- * path, and embedders with a fixed memory budget.  This call allocates
- * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
- * scratch is a fixed 288 KB array in device memory that every GPU which
- * loads the library holds until the process exits.
+ * Who needs it: frameworks that own the device allocator and forbid other
+ * code from calling cudaMalloc, real-time loops that may not allocate on the
+ * hot path (an allocation can block or fail at an arbitrary moment), and
+ * embedders with a fixed device-memory budget.  This call allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library routine.  Its scratch is
+ * a fixed 288 KB array in device memory that every GPU which loads the
+ * library holds until the process exits.
  *
  * dev_m: nx*ny*nz*10 elements of type dtype (LLB_F32 or LLB_F64), caller-owned.
  * stream: cudaStream_t (NULL = legacy default stream).  host_out: caller-owned
- * host struct, filled before the call returns (the call synchronises the
- * stream).  Limits: nx*ny*nz <= 67,108,864 nodes, else LLB_EINVAL and nothing
- * runs.  Every call shares the one scratch array: calls whose work overlaps
- * on the GPU (other streams, other host threads) race and must be ordered by
- * the caller.  The first call on a device looks up the scratch address with
- * that device current; make that first call before any stream capture.
+ * host struct, filled before the call returns (the call copies the result to
+ * it and synchronises the stream).  Limits: nx*ny*nz <= 67,108,864 nodes,
+ * else LLB_EINVAL and nothing runs.  Every call shares the one scratch array
+ * and each call overwrites the parts it reads, so nothing carries over from
+ * an earlier call; calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it and must be ordered by the caller.  The first call
+ * on a device looks up the array's device address with that device current
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use the call across a cudaDeviceReset of that
+ * device (the kept address then belongs to a context that no longer exists).
  * Returns LLB_OK, LLB_EINVAL or LLB_ECUDA. */
 LLB_API int llb_diagnostics_noalloc(const void* dev_m, int dtype, int nx, int ny, int nz, void* stream,
                                     llb_diag* host_out);
+
+/* Load canonical moments from HOST memory (element type host_dtype), advance
+ * nsteps >= 1 time steps and write the canonical moments after the last
+ * step into HOST memory: the same result as llb_init_moments + llb_step +
+ * llb_get_moments, with the host<->device copies overlapped with the device
+ * work.  The box is cut into slabs of whole z-planes; slab copies in,
+ * per-slab steps (each waits for the input slabs its pull reaches) and slab
+ * copies out run on three streams of the context, ordered by events, so the
+ * call takes about as long as the larger of the two host copies.  With
+ * nsteps > 1 only the first step overlaps the copies in and the last step
+ * the copies out.  One-component moment-only contexts on the tiled kernel;
+ * other contexts get the same result without the overlap.  Page-locked host
+ * buffers let the copies run asynchronously.  host_in and host_out stay
+ * owned by the caller and must not overlap.  Starts after the work already
+ * queued on the context stream and synchronises.  Returns LLB_EUNSTABLE
+ * (after the steps ran) if the input held rho <= 0 or a non-finite value. */
+LLB_API int llb_step_host(llb_ctx* ctx, const void* host_in, void* host_out, int host_dtype, int nsteps);
 
 /* Wait for all work of the context. */
 LLB_API int llb_synchronize(llb_ctx* ctx);

@@ -444,7 +444,7 @@ cudaError_t fwd_one(llb_ctx* c) {
     void* out = c->buf[1 - c->cur];
     const cudaError_t e = c->ncomp == 2                   ? launch_cg_tiled(*c, in, out)
                           : c->kernel == LLB_KERNEL_TMA   ? launch_moment_tma(*c, c->cur, out)
-                          : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
+                          : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, c->cur, in, out)
                                                           : launch_moment_direct(*c, in, out);
     if (e == cudaSuccess) c->cur = 1 - c->cur;
     return e;

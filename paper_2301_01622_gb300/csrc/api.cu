@@ -76,15 +76,14 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
         p.kernel != LLB_KERNEL_TMA) {
         *why = "unknown kernel"; return LLB_EINVAL;
     }
-    if (p.variant < 0 || p.variant > 9) { *why = "variant must be in 0..9"; return LLB_EINVAL; }
-    if (p.ncomp == 2 && p.variant > 1) { *why = "the two-component kernel has variants 0..1"; return LLB_EINVAL; }
+    if (p.variant < 0 || p.variant >= kTiledVariants32) { *why = "variant out of range"; return LLB_EINVAL; }
+    if (p.ncomp == 2 && p.variant >= kCGVariants) { *why = "two-component variant out of range"; return LLB_EINVAL; }
     if (p.wait_budget_ms < 1 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 1..600000"; return LLB_EINVAL; }
     if (p.debug_flags & ~1) { *why = "unknown debug flag"; return LLB_EINVAL; }
     if (!(p.grad_eps >= 0.0) || !std::isfinite(p.grad_eps)) { *why = "grad_eps must be finite and >= 0"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
-        if (p.scheme != LLB_SCHEME_MOMENT) { *why = "two components run only the moment-only scheme"; return LLB_EINVAL; }
         if (nx < 4 || ny < 4 || nz < 4) { *why = "two components need nx, ny, nz >= 4"; return LLB_EINVAL; }
-        if (p.kernel == LLB_KERNEL_DIRECT || p.kernel == LLB_KERNEL_TMA) {
+        if (p.scheme == LLB_SCHEME_MOMENT && (p.kernel == LLB_KERNEL_DIRECT || p.kernel == LLB_KERNEL_TMA)) {
             *why = "two components run the tiled kernel"; return LLB_EINVAL;
         }
         if (!(p.beta >= 0.0) || !std::isfinite(p.A_s) || !std::isfinite(p.A_h) || !(p.g_min > 0.0) || p.h_c < 0 ||
@@ -182,10 +181,10 @@ int check_bad_flag(llb_ctx* c) {
 cudaError_t launch_one(llb_ctx* c, int cur) {
     const void* in = c->buf[cur];
     void* out = c->buf[1 - cur];
-    if (c->ncomp == 2) return launch_cg_tiled(*c, in, out);
+    if (c->ncomp == 2 && c->scheme == LLB_SCHEME_MOMENT) return launch_cg_tiled(*c, in, out);
     if (c->scheme == LLB_SCHEME_MOMENT)
         return c->kernel == LLB_KERNEL_TMA     ? launch_moment_tma(*c, cur, out)
-               : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, in, out)
+               : c->kernel == LLB_KERNEL_TILED ? launch_moment_tiled(*c, cur, in, out)
                                                : launch_moment_direct(*c, in, out);
     return launch_population_step(*c, in, out, c->scheme == LLB_SCHEME_POPULATION_BGK);
 }
@@ -194,13 +193,14 @@ cudaError_t launch_one(llb_ctx* c, int cur) {
 bool configure(llb_ctx* c, int kernel, int variant) {
     c->kernel = kernel;
     c->variant = variant;
-    if (c->ncomp == 2) {
+    if (c->ncomp == 2 && c->scheme == LLB_SCHEME_MOMENT) {
         c->tile_ctas = cg_tiled_ctas(*c);
         cudaGetLastError();
         return kernel == LLB_KERNEL_TILED && c->tile_ctas > 0;
     }
     if (kernel == LLB_KERNEL_TILED) {
         c->tile_ctas = moment_tiled_ctas(*c);
+        c->pmap_ok = moment_tiled_encode(*c, c->buf[0], &c->pmap[0]) && moment_tiled_encode(*c, c->buf[1], &c->pmap[1]);
         cudaGetLastError();
         return c->tile_ctas > 0;
     }
@@ -316,6 +316,8 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
     if (cudaMalloc(&c->diag_scratch, c->diag_scratch_bytes + sizeof(llb_diag)) != cudaSuccess) { cudaGetLastError(); c->diag_scratch = nullptr; return bail(LLB_ENOMEM); }
     if (cudaMalloc(&c->flag_dev, 2 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); c->flag_dev = nullptr; return bail(LLB_ENOMEM); }
     c->err_dev = static_cast<int*>(c->flag_dev) + 1;
+    if (c->scheme != LLB_SCHEME_MOMENT && c->ncomp == 2 &&
+        cudaMalloc(&c->phi_scratch, c->N * c->elem) != cudaSuccess) { cudaGetLastError(); c->phi_scratch = nullptr; return bail(LLB_ENOMEM); }
     if (cudaMemsetAsync(c->flag_dev, 0, 2 * sizeof(int), c->stream) != cudaSuccess) { cudaGetLastError(); return bail(LLB_ECUDA); }
     if (c->scheme == LLB_SCHEME_MOMENT && c->ncomp == 2) {
         c->tile_ctas = cg_tiled_ctas(*c);
@@ -324,6 +326,7 @@ int llb_create(llb_ctx** out, int nx, int ny, int nz, int lattice, double tau, c
         c->kernel = LLB_KERNEL_TILED;
     } else if (c->scheme == LLB_SCHEME_MOMENT) {
         c->tile_ctas = moment_tiled_ctas(*c);
+        c->pmap_ok = moment_tiled_encode(*c, c->buf[0], &c->pmap[0]) && moment_tiled_encode(*c, c->buf[1], &c->pmap[1]);
         cudaGetLastError();
         c->tmap_ok = moment_tma_encode(*c, c->buf[0], &c->tmap[0]) && moment_tma_encode(*c, c->buf[1], &c->tmap[1]);
         c->tma_ctas = c->tmap_ok ? moment_tma_ctas(*c) : 0;
@@ -350,6 +353,10 @@ void llb_destroy(llb_ctx* c) {
     if (c->staging) cudaFree(c->staging);
     if (c->diag_scratch) cudaFree(c->diag_scratch);
     if (c->flag_dev) cudaFree(c->flag_dev);
+    if (c->phi_scratch) cudaFree(c->phi_scratch);
+    if (c->staging_out) cudaFree(c->staging_out);
+    for (int k = 0; k < 3; ++k)
+        if (c->pipe[k]) cudaStreamDestroy(c->pipe[k]);
     drop_graphs(c);
     cudaGetLastError();
     delete c;
@@ -462,10 +469,11 @@ int llb_autotune(llb_ctx* c, int trials, int* kernel, int* variant) {
     struct Cand { int kernel, variant; };
     Cand cands[24];
     int nc = 0;
-    const int nvar = c->ncomp == 2 ? 2 : 10;
+    const int nvar = c->ncomp == 2 ? kCGVariants : (c->storage == LLB_F32 ? kTiledVariants32 : 1);
     for (int v = 0; v < nvar; ++v) cands[nc++] = {LLB_KERNEL_TILED, v};
     if (c->ncomp == 1) {
-        for (int v = 0; v < 5; ++v) cands[nc++] = {LLB_KERNEL_TMA, v};
+        const int ntma = c->storage == LLB_F32 ? kTmaVariants : (c->storage == LLB_F64 ? 1 : 0);
+        for (int v = 0; v < ntma; ++v) cands[nc++] = {LLB_KERNEL_TMA, v};
         cands[nc++] = {LLB_KERNEL_DIRECT, 0};
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;

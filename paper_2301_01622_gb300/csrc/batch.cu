@@ -105,7 +105,8 @@ extern "C" {
 int llb_batch_create(llb_batch** out, int ndomains, const int* dims, int lattice, double tau, const llb_params* p) {
     if (!out) return LLB_EINVAL;
     *out = nullptr;
-    if (ndomains < 1 || ndomains > 65536 || !dims || !p || p->ncomp != 2) return LLB_EINVAL;
+    if (ndomains < 1 || ndomains > 65536 || !dims || !p || p->ncomp != 2 || p->scheme != LLB_SCHEME_MOMENT)
+        return LLB_EINVAL;
     llb_batch* b = new (std::nothrow) llb_batch();
     if (!b) return LLB_ENOMEM;
     b->n = ndomains;
@@ -232,7 +233,7 @@ int llb_batch_autotune(llb_batch* b, int trials, int* variant) {
     const int keep = b->variant;
     float best = -1.0f;
     int win = keep;
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < llb::kCGVariants; ++v) {
         b->variant = v;
         if (build_tables(b) != LLB_OK) continue;
         // each trial recomputes the current step into the spare copies: the state does not move

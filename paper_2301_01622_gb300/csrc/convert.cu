@@ -12,6 +12,8 @@
 // write to it also writes the node's ghost copies.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
@@ -52,11 +54,12 @@ __device__ __forceinline__ void put(T* __restrict__ st, const Layout& L, int x, 
     });
 }
 
+// Nodes i0 .. i1-1 of the dense canonical order (whole planes for a z-range).
 template <class T>
 __global__ void k_canon_to_shifted(const void* __restrict__ canon, int cdt, T* __restrict__ st, Layout L,
-                                   int* bad) {
+                                   int* bad, size_t i0, size_t i1) {
     const size_t N = (size_t)L.nx * L.ny * L.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < i1; i += (size_t)gridDim.x * blockDim.x) {
         double v[10];
 #pragma unroll
         for (int f = 0; f < 10; ++f) v[f] = rdt(canon, f * N + i, cdt);
@@ -74,9 +77,10 @@ __global__ void k_canon_to_shifted(const void* __restrict__ canon, int cdt, T* _
 }
 
 template <class T>
-__global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L) {
+__global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L, size_t i0,
+                                   size_t i1) {
     const size_t N = (size_t)L.nx * L.ny * L.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < i1; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         decode(L, i, x, y, z);
         const size_t j = L.at(x, y, z);
@@ -181,12 +185,12 @@ int grid_for(const llb_ctx& c) {
 
 cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int cdt, void* st, int* bad) {
     if (c.storage == LLB_F16S) {
-        k_canon_to_shifted<__half><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<__half*>(st), c.lay, bad);
+        k_canon_to_shifted<__half><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<__half*>(st), c.lay, bad, 0, c.N);
         return cudaGetLastError();
     }
     if (c.storage == LLB_BF16S) {
         k_canon_to_shifted<__nv_bfloat16><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<__nv_bfloat16*>(st),
-                                                                             c.lay, bad);
+                                                                             c.lay, bad, 0, c.N);
         return cudaGetLastError();
     }
     if (c.ncomp == 2) {
@@ -197,20 +201,22 @@ cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int
         return cudaGetLastError();
     }
     if (c.storage == LLB_F64)
-        k_canon_to_shifted<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
+        k_canon_to_shifted<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad,
+                                                                       0, c.N);
     else
-        k_canon_to_shifted<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad);
+        k_canon_to_shifted<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad,
+                                                                      0, c.N);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* canon, int cdt) {
     if (c.storage == LLB_F16S) {
-        k_shifted_to_canon<__half><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const __half*>(st), canon, cdt, c.lay);
+        k_shifted_to_canon<__half><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const __half*>(st), canon, cdt, c.lay, 0, c.N);
         return cudaGetLastError();
     }
     if (c.storage == LLB_BF16S) {
         k_shifted_to_canon<__nv_bfloat16><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const __nv_bfloat16*>(st), canon,
-                                                                             cdt, c.lay);
+                                                                             cdt, c.lay, 0, c.N);
         return cudaGetLastError();
     }
     if (c.ncomp == 2) {
@@ -221,9 +227,53 @@ cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* 
         return cudaGetLastError();
     }
     if (c.storage == LLB_F64)
-        k_shifted_to_canon<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
+        k_shifted_to_canon<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay,
+                                                                       0, c.N);
     else
-        k_shifted_to_canon<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay);
+        k_shifted_to_canon<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay,
+                                                                      0, c.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_canonical_to_shifted_range(const llb_ctx& c, const void* canon, int cdt, void* st, int* bad, int zlo,
+                                              int zhi, cudaStream_t s) {
+    const size_t per = (size_t)c.nx * c.ny, i0 = per * zlo, i1 = per * zhi;
+    const int grid = (int)std::min<size_t>((i1 - i0 + 255) / 256, (size_t)c.num_sms * 8);
+    switch (c.storage) {
+        case LLB_F64:
+            k_canon_to_shifted<double><<<grid, 256, 0, s>>>(canon, cdt, static_cast<double*>(st), c.lay, bad, i0, i1);
+            break;
+        case LLB_F16S:
+            k_canon_to_shifted<__half><<<grid, 256, 0, s>>>(canon, cdt, static_cast<__half*>(st), c.lay, bad, i0, i1);
+            break;
+        case LLB_BF16S:
+            k_canon_to_shifted<__nv_bfloat16><<<grid, 256, 0, s>>>(canon, cdt, static_cast<__nv_bfloat16*>(st), c.lay,
+                                                                  bad, i0, i1);
+            break;
+        default:
+            k_canon_to_shifted<float><<<grid, 256, 0, s>>>(canon, cdt, static_cast<float*>(st), c.lay, bad, i0, i1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shifted_to_canonical_range(const llb_ctx& c, const void* st, void* canon, int cdt, int zlo, int zhi,
+                                              cudaStream_t s) {
+    const size_t per = (size_t)c.nx * c.ny, i0 = per * zlo, i1 = per * zhi;
+    const int grid = (int)std::min<size_t>((i1 - i0 + 255) / 256, (size_t)c.num_sms * 8);
+    switch (c.storage) {
+        case LLB_F64:
+            k_shifted_to_canon<double><<<grid, 256, 0, s>>>(static_cast<const double*>(st), canon, cdt, c.lay, i0, i1);
+            break;
+        case LLB_F16S:
+            k_shifted_to_canon<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(st), canon, cdt, c.lay, i0, i1);
+            break;
+        case LLB_BF16S:
+            k_shifted_to_canon<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(st), canon, cdt,
+                                                                  c.lay, i0, i1);
+            break;
+        default:
+            k_shifted_to_canon<float><<<grid, 256, 0, s>>>(static_cast<const float*>(st), canon, cdt, c.lay, i0, i1);
+    }
     return cudaGetLastError();
 }
 

@@ -30,8 +30,10 @@ struct llb_ctx {
     size_t state_bytes = 0;  // bytes of one state copy
     llb::Layout lay{};       // layout of moment-format buffers (state of the moment scheme,
                              // temporaries of the population schemes)
-    CUtensorMap tmap[2];     // TMA descriptors of buf[0], buf[1] (moment scheme)
+    CUtensorMap tmap[2];     // TMA stage-load descriptors of buf[0], buf[1] (TMA kernel)
     bool tmap_ok = false;
+    CUtensorMap pmap[2];     // TMA L2-prefetch descriptors of buf[0], buf[1] (tiled kernel)
+    bool pmap_ok = false;
     void* err_dev = nullptr; // device int: set by a kernel whose bounded wait gave up
     void* buf[2] = {nullptr, nullptr};
     bool owns[2] = {false, false};
@@ -39,6 +41,10 @@ struct llb_ctx {
     void* staging = nullptr; // canonical moments (FP64 worst case) for host/device conversion
     size_t staging_bytes = 0;
     void* diag_scratch = nullptr;  // per-block partial sums of the diagnostics
+    void* phi_scratch = nullptr;   // phase field of the two-component population schemes (N elements)
+    void* staging_out = nullptr;   // canonical output of the pipelined host step (llb_step_host)
+    size_t staging_out_bytes = 0;
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};  // copy-in, step, copy-out streams of llb_step_host
     size_t diag_scratch_bytes = 0;
     void* flag_dev = nullptr;      // device int for init-time checks
     long long t = 0;
@@ -59,16 +65,44 @@ size_t elem_size(int dtype);
 int fields_of(const llb_ctx& c);           // arrays per state copy
 int canonical_fields(const llb_ctx& c);    // 10 or 11
 
-// Moment-only, one component (moment_step.cu)
+// Moment-only, one component (moment_step.cu, moment_tiled_*.cu, moment_tma.cu).
+// in_index: which of the context's buffers is the input (selects the TMA map).
+constexpr int kTiledVariants32 = 6;  // variants of the FP32 tiled kernel (other storage types: 1)
+constexpr int kTmaVariants = 3;      // variants of the TMA kernel
 cudaError_t launch_moment_direct(const llb_ctx& c, const void* in, void* out);
-cudaError_t launch_moment_tiled(const llb_ctx& c, const void* in, void* out);
+cudaError_t launch_moment_tiled(const llb_ctx& c, int in_index, const void* in, void* out);
+// Output planes zlo .. zhi-1 only, on stream st (the pipelined host step).
+cudaError_t launch_moment_tiled_range(const llb_ctx& c, int in_index, const void* in, void* out, int zlo, int zhi,
+                                      cudaStream_t st);
 cudaError_t launch_moment_tma(const llb_ctx& c, int in_index, void* out);
 int moment_tiled_ctas(const llb_ctx& c);   // persistent grid size, 0 if the kernel cannot run
 int moment_tma_ctas(const llb_ctx& c);
-// Encode the TMA descriptor of a moment buffer; false if TMA cannot serve this shape.
+// Encode the TMA stage-load descriptor of a moment buffer; false if TMA cannot serve this shape.
 bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out);
+// Encode the L2-prefetch descriptor of the tiled kernel's box for a moment buffer.
+bool moment_tiled_encode(const llb_ctx& c, void* buf, CUtensorMap* out);
+// 4D (x, y, z, field) tensor map of a padded moment state, box_w x box_h nodes x 10 fields.
+bool encode_box_map(const llb_ctx& c, void* buf, int box_w, int box_h, CUtensorMap* out);
+// Per storage type (moment_tiled_<type>.cu)
+int moment_tiled_ctas_f32(const llb_ctx& c);
+int moment_tiled_ctas_f64(const llb_ctx& c);
+int moment_tiled_ctas_f16(const llb_ctx& c);
+int moment_tiled_ctas_bf16(const llb_ctx& c);
+cudaError_t launch_moment_tiled_f32(const llb_ctx& c, int in_index, const void* in, void* out, int zlo, int zhi,
+                                     cudaStream_t st);
+cudaError_t launch_moment_tiled_f64(const llb_ctx& c, int in_index, const void* in, void* out, int zlo, int zhi,
+                                     cudaStream_t st);
+cudaError_t launch_moment_tiled_f16(const llb_ctx& c, int in_index, const void* in, void* out, int zlo, int zhi,
+                                     cudaStream_t st);
+cudaError_t launch_moment_tiled_bf16(const llb_ctx& c, int in_index, const void* in, void* out, int zlo, int zhi,
+                                     cudaStream_t st);
+void moment_tiled_box_f32(const llb_ctx& c, int* w, int* h);
+void moment_tiled_box_f64(const llb_ctx& c, int* w, int* h);
+void moment_tiled_box_f16(const llb_ctx& c, int* w, int* h);
+void moment_tiled_box_bf16(const llb_ctx& c, int* w, int* h);
 
 // Two-component colour-gradient moment-only step (cg_step.cu)
+constexpr int kCGVariants = 4;  // tile / division variants of the two-component kernel
 int cg_tiled_ctas(const llb_ctx& c);
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out);
 
@@ -97,6 +131,11 @@ cudaError_t launch_moments_from_population(const llb_ctx& c, const void* state, 
 cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int canon_dtype, void* state,
                                         int* bad_flag);
 cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* state, void* canon, int canon_dtype);
+// One component: planes zlo .. zhi-1 only, on stream st.
+cudaError_t launch_canonical_to_shifted_range(const llb_ctx& c, const void* canon, int canon_dtype, void* state,
+                                              int* bad_flag, int zlo, int zhi, cudaStream_t st);
+cudaError_t launch_shifted_to_canonical_range(const llb_ctx& c, const void* state, void* canon, int canon_dtype,
+                                              int zlo, int zhi, cudaStream_t st);
 cudaError_t launch_equilibrium(const llb_ctx& c, const void* rho, const void* u, int dtype, void* state,
                                int* bad_flag);
 

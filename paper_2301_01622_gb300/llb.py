@@ -73,6 +73,7 @@ _SIGS = {
     "llb_step_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "llb_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "llb_get_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "llb_step_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "llb_get_moments_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "llb_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(llb_diag)]),
     "llb_synchronize": (C.c_int, [C.c_void_p]),
@@ -244,6 +245,16 @@ def llb_adjoint(ctx, nsteps, gfinal_dev, ginit_dev, every: int = 0) -> float:
 
 def llb_get_moments(ctx, host_out):
     _check(lib().llb_get_moments(ctx, _ptr(host_out), _dtype_code(host_out)), "llb_get_moments", ctx)
+    return host_out
+
+
+def llb_step_host(ctx, host_in, host_out, nsteps=1):
+    """Host moments in, nsteps steps, host moments out, with the copies
+    overlapped with the device work (see include/llb.h)."""
+    dt = _dtype_code(host_in)
+    if _dtype_code(host_out) != dt:
+        raise TypeError("host_in and host_out must have the same dtype")
+    _check(lib().llb_step_host(ctx, _ptr(host_in), _ptr(host_out), dt, int(nsteps)), "llb_step_host", ctx)
     return host_out
 
 

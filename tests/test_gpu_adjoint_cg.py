@@ -149,3 +149,51 @@ def test_autograd_wrapper_two_components(case):
     L.backward()
     np.testing.assert_allclose(m.grad.cpu().numpy(), g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
     assert abs(float(tau.grad) - dtau) <= 1e-9 * abs(dtau)
+
+
+def test_gradient_vs_oracle_finite_differences():
+    """Reference gradient from the FP64 oracle: central differences of the
+    oracle's two-component moment-only runs (smooth normal, eps > 0, no
+    near-contact force) for a linear functional of the final phase field,
+    J = sum w phi(t_N), on a 12^3 off-axis pair, against llb_adjoint's
+    gradient with respect to the initial j, rho1 and tau."""
+    from oracle import D3Q27
+    from oracle import two_component as tc
+
+    n, steps, tau = 12, 6, 0.9
+    c1 = (n / 2 - 3.5, n / 2 - 0.5, n / 2)
+    c2 = (n / 2 + 3.5, n / 2 + 0.5, n / 2)
+    r1, r2, u = inputs.droplets(n, n, n, [c1, c2], [2.5, 2.5], [(0.04, 0, 0), (-0.04, 0, 0)])
+    tot = lb.equilibrium_moments(r1 + r2, u)
+    m0 = np.ascontiguousarray(np.concatenate([r1[None], r2[None], tot[1:]]))
+    w = np.random.default_rng(3).standard_normal((n, n, n))
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.0, eps=0.02)
+
+    def J(m, t):
+        out = tc.run_moment_only(m, D3Q27, t, prm, steps)
+        return float((w * (out[0] - out[1]) / (out[0] + out[1])).sum())
+
+    # dJ/dm at the final state: phi = (rho1 - rho2)/(rho1 + rho2)
+    fin = tc.run_moment_only(m0, D3Q27, tau, prm, steps)
+    rho = fin[0] + fin[1]
+    gN = np.zeros_like(fin)
+    gN[0] = w * 2 * fin[1] / rho ** 2
+    gN[1] = -w * 2 * fin[0] / rho ** 2
+    ctx = llb.llb_create(n, n, n, 27, tau, llb.llb_params_default(storage=llb.LLB_F64, **PRM))
+    try:
+        llb.llb_init_moments(ctx, m0)
+        gi = torch.empty((11, n, n, n), dtype=torch.float64, device="cuda")
+        dtau = llb.llb_adjoint(ctx, steps, torch.from_numpy(gN).cuda(), gi, every=2)
+    finally:
+        llb.llb_destroy(ctx)
+    gi = gi.cpu().numpy()
+    eps = 1e-6
+    # interface and bulk nodes; fields rho1, rho2, j_x, j_y, P_xy
+    for (f, z, y, x) in [(0, 6, 5, 3), (0, 6, 6, 9), (1, 5, 6, 4), (2, 6, 5, 2), (3, 6, 6, 8), (2, 0, 0, 0), (8, 6, 6, 6)]:
+        mp, mm = m0.copy(), m0.copy()
+        mp[f, z, y, x] += eps
+        mm[f, z, y, x] -= eps
+        fd = (J(mp, tau) - J(mm, tau)) / (2 * eps)
+        assert abs(fd - gi[f, z, y, x]) <= 1e-5 * max(abs(fd), 0.1), (f, z, y, x, fd, gi[f, z, y, x])
+    fd = (J(m0, tau + eps) - J(m0, tau - eps)) / (2 * eps)
+    assert abs(fd - dtau) <= 1e-5 * max(abs(fd), 0.1)

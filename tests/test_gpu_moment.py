@@ -51,8 +51,8 @@ def test_taylor_green_fp32_200_steps(q, kernel):
     """Same run with FP32 storage and arithmetic: 1e-5 after 200 steps."""
     n, tau = 32, 0.8
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05)
-    # the default FP32 TMA tile (64 x 4) is wider than this box; variant 3 is 32 x 8
-    variant = 3 if kernel == llb.LLB_KERNEL_TMA else 0
+    # the default FP32 TMA tile (64 x 4) is wider than this box; variant 2 is 32 x 8
+    variant = 2 if kernel == llb.LLB_KERNEL_TMA else 0
     got, used = run_gpu((n, n, n), q, tau, 200, rho=rho, u=u, storage=llb.LLB_F32, kernel=kernel, variant=variant)
     assert used == kernel
     assert_groups(got, oracle_tg(q, n, tau, 200, 0.0), 1e-5, what=f"D3Q{q} fp32")
@@ -96,7 +96,7 @@ def _oracle_ragged(q):
     return lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 20)
 
 
-KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL_TILED, v) for v in range(10)]
+KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(3)] + [(llb.LLB_KERNEL_TILED, v) for v in range(6)]
 
 
 @pytest.mark.parametrize("kernel, variant", KERNEL_VARIANTS,
@@ -104,7 +104,7 @@ KERNEL_VARIANTS = [(llb.LLB_KERNEL_TMA, v) for v in range(5)] + [(llb.LLB_KERNEL
 @pytest.mark.parametrize("q", [19, 27])
 def test_kernel_variants_match_oracle(variant, kernel, q):
     """Every tuning variant of the z-marching kernels (tile shape, ring depth,
-    CTAs/SM, split-phase plane barrier, approximate 1/rho, halo warps) computes the same
+    CTAs/SM, split-phase plane barrier, approximate 1/rho, L2 prefetch) computes the same
     step: ragged multi-tile box, FP32, 1e-5 after 20 steps."""
     shape = (133, 37, 29)
     rho, u = inputs.taylor_green_3d(*shape, u0=0.05, noise=1e-3, seed=7)
@@ -118,10 +118,13 @@ def test_kernel_variants_match_oracle(variant, kernel, q):
     assert_groups(got, _oracle_ragged(q), 1e-5, what=f"variant {variant}")
 
 
-def test_tma_kernel_has_five_variants():
-    """Variants 5..9 exist for the plain-load kernel only: asking the TMA
-    kernel for one is refused at creation."""
-    p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, variant=5)
+def test_tma_kernel_has_three_variants():
+    """Variants 3..5 exist for the plain-load kernel only: asking the TMA
+    kernel for one is refused at creation, and variant 6 for either kernel."""
+    with pytest.raises(llb.LLBError) as e:
+        llb.llb_create(64, 64, 64, 19, 0.8, llb.llb_params_default(kernel=llb.LLB_KERNEL_TILED, variant=6))
+    assert e.value.status == llb.LLB_EINVAL
+    p = llb.llb_params_default(kernel=llb.LLB_KERNEL_TMA, variant=3)
     with pytest.raises(llb.LLBError) as e:
         llb.llb_create(64, 64, 64, 19, 0.8, p)
     assert e.value.status == llb.LLB_EINVAL
@@ -138,8 +141,8 @@ def test_zero_steps_round_trip(q):
 def test_tiled_is_deterministic_and_matches_direct(q):
     n = 40
     rho, u = inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=5)
-    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=3)
-    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=3)
+    a, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=2)
+    b, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TMA, variant=2)
     c, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_TILED)
     d, _ = run_gpu((n, n, n), q, 0.6, 20, rho=rho, u=u, storage=llb.LLB_F32, kernel=llb.LLB_KERNEL_DIRECT)
     assert np.array_equal(a, b)
@@ -342,3 +345,57 @@ def test_autotune_keeps_state(q):
         llb.llb_destroy(ctx)
     ref = lb.run_moment_only(lb.equilibrium_moments(rho, u), LAT[q], 0.7, 5)
     assert_groups(got, ref, 1e-5, what=f"autotuned kernel {kernel} variant {variant}")
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+@pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("shape", [(64, 48, 40), (67, 45, 37), (33, 9, 5)], ids=lambda s: "x".join(map(str, s)))
+def test_step_host_matches_sequential(shape, storage, nsteps):
+    """llb_step_host (copies overlapped with per-slab steps) gives bit for bit
+    what llb_init_moments + llb_step + llb_get_moments give."""
+    nx, ny, nz = shape
+    m0 = inputs.random_moments(nx, ny, nz, seed=nx + ny + nz)
+    hdt = np.float32 if storage == llb.LLB_F32 else np.float64
+    h_in = np.ascontiguousarray(m0.astype(hdt))
+    out = []
+    for piped in (False, True):
+        ctx = llb.llb_create(nx, ny, nz, 19, 0.7, llb.llb_params_default(storage=storage))
+        try:
+            res = np.empty_like(h_in)
+            if piped:
+                llb.llb_step_host(ctx, h_in, res, nsteps)
+            else:
+                llb.llb_init_moments(ctx, h_in)
+                llb.llb_step(ctx, nsteps)
+                llb.llb_get_moments(ctx, res)
+            assert llb.llb_steps_done(ctx) == nsteps
+            # the context holds the stepped state afterwards
+            again = llb.llb_get_moments(ctx, np.empty_like(h_in))
+        finally:
+            llb.llb_destroy(ctx)
+        assert np.array_equal(again, res)
+        out.append(res)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_step_host_rejects_unphysical_input_and_other_kernels_fall_back():
+    """rho <= 0 in the input is reported as LLB_EUNSTABLE; a context on the
+    direct kernel takes the non-overlapped path and gives the same result."""
+    n = 16
+    m0 = inputs.random_moments(n, n, n, seed=5)
+    bad = m0.copy()
+    bad[0, 2, 3, 4] = -1.0
+    ctx = llb.llb_create(n, n, n, 19, 0.8, llb.llb_params_default(storage=llb.LLB_F64))
+    try:
+        with pytest.raises(llb.LLBError) as e:
+            llb.llb_step_host(ctx, bad, np.empty_like(bad), 1)
+        assert e.value.status == llb.LLB_EUNSTABLE
+        good = llb.llb_step_host(ctx, m0, np.empty_like(m0), 2)
+    finally:
+        llb.llb_destroy(ctx)
+    ctx = llb.llb_create(n, n, n, 19, 0.8, llb.llb_params_default(storage=llb.LLB_F64, kernel=llb.LLB_KERNEL_DIRECT))
+    try:
+        direct = llb.llb_step_host(ctx, m0, np.empty_like(m0), 2)
+    finally:
+        llb.llb_destroy(ctx)
+    assert_groups(direct, good, 1e-14, what="direct vs tiled host step")

@@ -2,8 +2,10 @@
 arithmetic) against the FP64 oracle.  The bounds are measured errors of this
 implementation rounded up, stated per moment group (rho; j; P) as
 max |gpu - oracle| / max |oracle| over the group after 200 steps of the 32^3
-Taylor-Green vortex (u0 = 0.05, tau = 0.8), and after one step of the full
-256^3 bench field."""
+Taylor-Green vortex (u0 = 0.05, tau = 0.8).  The per-field bounds after 200
+steps of the bench field on a multi-tile box are in test_gpu_parity_fields.py,
+and bench.py reports the per-field errors after one step of the full 256^3
+bench field."""
 import functools
 
 import numpy as np

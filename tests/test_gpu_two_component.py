@@ -9,7 +9,7 @@ from oracle import D3Q19, D3Q27, lb
 from oracle import two_component as tc
 from paper_2301_01622_gb300 import inputs, llb
 
-from gpu_helpers import assert_groups, run_gpu
+from gpu_helpers import assert_fields, assert_groups, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -60,22 +60,50 @@ def test_droplet_pair_fp64(q, A_h):
 
 
 @pytest.mark.parametrize("q", [19, 27])
-def test_tile_variant_32x8(q):
-    """The 32 x 8 tile variant computes the same step as the default 64 x 4 one."""
+def test_tile_variant_64x4_fp64(q):
+    """FP64 has one tile shape; asking for another variant runs that same shape
+    and gives the same step (1e-12)."""
     shape, steps, tau = (40, 24, 20), 20, 0.9
     ref = _oracle_pair(q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, 0.01, 1e-8)
     r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
     prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.01, h_c=3, g_min=1e-8)
     got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, variant=1, **_params(prm, llb.LLB_F64))
-    assert_groups(got, ref, 1e-12, GROUPS_2, what=f"D3Q{q} 32x8")
+    assert_groups(got, ref, 1e-12, GROUPS_2, what=f"D3Q{q} variant 1")
+
+
+# An off-axis pair that approaches but does not touch within 100 steps: FP32
+# parity is checked away from coalescence, because the thinning neck of a
+# merging pair amplifies rounding differences (the FP64 tests above cover a
+# pair that touches).
+APART = ((48, 24, 20), 5.0, 10.0, 0.02, 2.0)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3], ids=["32x8-fast", "64x4", "32x8", "32x16"])
+@pytest.mark.parametrize("q", [19, 27])
+def test_tile_variants_fp32(q, variant):
+    """Every FP32 variant of the two-component kernel (tile 32 x 8 with
+    approximate FP32 quotients for phi, 1/rho and 1/|G| -- the default --,
+    and 64 x 4, 32 x 8, 32 x 16 with IEEE quotients)
+    computes the same step: approaching off-axis pair, 100 steps, within
+    1e-5 of the FP64 oracle per shifted field."""
+    shape, radius, gap, speed, impact = APART
+    steps, tau = 100, 0.9
+    ref = _oracle_pair(q, shape, radius, gap, speed, impact, tau, steps, 0.0, 1e-8)
+    r1, r2, u = _pair(shape, radius, gap, speed, impact)
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.0, h_c=3)
+    got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, variant=variant,
+                     **_params(prm, llb.LLB_F32))
+    assert_fields(got, ref, 1e-5, what=f"D3Q{q} variant {variant}")
 
 
 @pytest.mark.parametrize("q", [19, 27])
 def test_droplet_pair_fp32(q):
-    """Same pair without the near-contact decision, FP32 storage, 100 steps: 1e-5."""
-    shape, steps, tau = (40, 24, 20), 100, 0.9
-    ref = _oracle_pair(q, shape, 5.0, 2.5, 0.03, 2.0, tau, steps, 0.0, 1e-8)
-    r1, r2, u = _pair(shape, 5.0, 2.5, 0.03, 2.0)
+    """FP32 storage, no near-contact decision, the approaching pair, 100 steps:
+    1e-5 per moment group."""
+    shape, radius, gap, speed, impact = APART
+    steps, tau = 100, 0.9
+    ref = _oracle_pair(q, shape, radius, gap, speed, impact, tau, steps, 0.0, 1e-8)
+    r1, r2, u = _pair(shape, radius, gap, speed, impact)
     prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=0.0, h_c=3)
     got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, **_params(prm, llb.LLB_F32))
     assert_groups(got, ref, 1e-5, GROUPS_2, what=f"D3Q{q} fp32")
