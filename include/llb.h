@@ -103,8 +103,10 @@ typedef struct llb_params {
                          64x8 and 32x8 tiles, split-phase plane barrier),
                          TMA kernel 0..2 (ring depth, tile); the other
                          storage types have one shape per kernel.  Two
-                         components 0..3 (tiles 32x8, 64x4, 32x8 with
-                         approximate FP32 quotients, 32x16).  A variant the
+                         components, FP32: 0..5 (tile 32x8 with approximate
+                         FP32 quotients and a rolled plane loop; 64x4, 32x8,
+                         32x16 with IEEE quotients; 32x8 approximate
+                         unrolled; 64x4 approximate rolled).  A variant the
                          kernel does not have is LLB_EINVAL.  Every variant
                          computes the same step (to FP32 rounding)           */
     /* two-component colour-gradient / near-contact parameters (Sec. III A-B) */

@@ -10,7 +10,7 @@ using namespace cg;
 template <class L, class T, class V>
 int cg_batch_ctas_v(const llb_ctx& c) {
     using C = CGCfg<L, T, V::BX, V::BY>;
-    auto kern = k_cg_batch<L, T, V::BX, V::BY, V::MINB, V::FAST>;
+    auto kern = k_cg_batch<L, T, V::BX, V::BY, V::MINB, V::FAST, V::ROLLED>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
@@ -32,7 +32,7 @@ void cg_batch_plan_v(const llb_ctx& c, int grid, BatchDom* d) {
 template <class L, class T, class V>
 cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid) {
     using C = CGCfg<L, T, V::BX, V::BY>;
-    k_cg_batch<L, T, V::BX, V::BY, V::MINB, V::FAST><<<grid, C::NT, C::smem_bytes, c.stream>>>(
+    k_cg_batch<L, T, V::BX, V::BY, V::MINB, V::FAST, V::ROLLED><<<grid, C::NT, C::smem_bytes, c.stream>>>(
         doms, ndom, total, cg_params<T>(c));
     return cudaGetLastError();
 }

@@ -10,7 +10,7 @@ using namespace cg;
 template <class L, class T, class V>
 int cg_ctas_v(const llb_ctx& c) {
     using C = CGCfg<L, T, V::BX, V::BY>;
-    auto kern = k_cg_tiled<L, T, V::BX, V::BY, V::MINB, V::FAST>;
+    auto kern = k_cg_tiled<L, T, V::BX, V::BY, V::MINB, V::FAST, V::ROLLED>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) != cudaSuccess)
         return 0;
     int per_sm = 0;
@@ -26,7 +26,7 @@ cudaError_t cg_run_v(const llb_ctx& c, const void* in, void* out) {
     using C = CGCfg<L, T, V::BX, V::BY>;
     const int grid = c.tile_ctas > 0 ? c.tile_ctas : 1;
     const Sched2 sc = plan2(c.nx, c.ny, c.nz, V::BX, V::BY, grid);
-    k_cg_tiled<L, T, V::BX, V::BY, V::MINB, V::FAST><<<grid, C::NT, C::smem_bytes, c.stream>>>(
+    k_cg_tiled<L, T, V::BX, V::BY, V::MINB, V::FAST, V::ROLLED><<<grid, C::NT, C::smem_bytes, c.stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), c.lay, cg_params<T>(c), sc);
     return cudaGetLastError();
 }

@@ -102,7 +102,7 @@ void moment_tiled_box_f16(const llb_ctx& c, int* w, int* h);
 void moment_tiled_box_bf16(const llb_ctx& c, int* w, int* h);
 
 // Two-component colour-gradient moment-only step (cg_step.cu)
-constexpr int kCGVariants = 4;  // tile / division variants of the two-component kernel
+constexpr int kCGVariants = 6;  // tile / division variants of the two-component kernel
 int cg_tiled_ctas(const llb_ctx& c);
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out);
 

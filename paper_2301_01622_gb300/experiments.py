@@ -9,11 +9,14 @@ returns on the host; no lattice-Boltzmann arithmetic happens here.
 * ``laplace_sweep`` -- static droplets of several radii: the pressure jump
   dp = cs^2 (rho_in - rho_out) against 1/R (Laplace's law dp = 2 sigma / R in
   three dimensions) gives the surface tension of the colour-gradient model.
+* ``viscosity_sweep`` -- a shear wave in a uniform mixture (no interface) of
+  the two-component step: its decay rate gives the mixture viscosity, to be
+  compared with nu = cs^2 (tau - 1/2) (Sec. III B).
 * ``local_error_curves`` -- the local relative error |rho_N - rho_P| / rho_N,max
   between the scheme without populations (N) and the standard scheme with
   populations (P) at the probe sites of Fig. 3 (Sec. IV).
 
-Run ``python -m paper_2301_01622_gb300.experiments outcome|laplace|e3`` to
+Run ``python -m paper_2301_01622_gb300.experiments outcome|laplace|viscosity|e3`` to
 print the records as JSON.
 """
 from __future__ import annotations
@@ -167,6 +170,35 @@ def laplace_sweep(radii=(8.0, 10.0, 12.0, 16.0, 20.0), n=80, steps=6000, lattice
             "lattice": lattice, "tau": tau, "A_s": A_s, "beta": beta}
 
 
+def viscosity_sweep(taus=(0.6, 0.8, 1.0, 1.5), n=64, steps=600, u0=1e-3, lattice=19, storage=llb.LLB_F64):
+    """Two-dimensional Taylor-Green cell (uniform along z) in a uniform
+    mixture rho1 = rho2 = 1/2: u decays as exp(-2 nu k^2 t).  The fitted
+    decay of the velocity amplitude over [steps/4, steps] gives nu."""
+    rows = []
+    k = 2 * np.pi / n
+    rho, u = inputs.shear_wave_2d(n, n, 4, u0=u0)
+    rho12 = np.stack([0.5 * rho, 0.5 * rho])
+    for tau in taus:
+        ctx = _ctx((n, n, 4), lattice, tau, ncomp=2, storage=storage, A_h=0.0)
+        ts, amps = [], []
+        try:
+            llb.llb_init_equilibrium(ctx, rho12, u)
+            t = 0
+            for t_next in np.linspace(steps // 4, steps, 7).astype(int):
+                llb.llb_step(ctx, int(t_next - t))
+                t = int(t_next)
+                m = llb.llb_get_moments(ctx, np.empty((11, 4, n, n)))
+                ux = m[2] / (m[0] + m[1])
+                ts.append(t)
+                amps.append(float(np.abs(ux).max()))
+        finally:
+            llb.llb_destroy(ctx)
+        slope = np.polyfit(np.array(ts, dtype=float), np.log(np.array(amps)), 1)[0]
+        nu = -slope / (2 * k * k)
+        rows.append({"tau": tau, "nu": nu, "nu_theory": CS2 * (tau - 0.5), "rel_err": nu / (CS2 * (tau - 0.5)) - 1})
+    return {"rows": rows, "n": n, "steps": steps, "lattice": lattice}
+
+
 def local_error_curves(ncomp=2, shape=(128, 128, 128), steps=3000, every=50, lattice=19, tau=1.0, A_h=0.05,
                        A_s=0.01, beta=0.7, radius=15.0, speed=0.05, impact=12.75, storage=llb.LLB_F32):
     """|rho_N - rho_P| / rho_N,max at the three probe sites, every `every`
@@ -220,10 +252,13 @@ def main(argv):
         out = [droplet_outcome(a) for a in (0.0, 0.01, 0.05)]
     elif what == "laplace":
         out = [laplace_sweep(lattice=q) for q in (19, 27)]
+        out += [laplace_sweep(lattice=19, A_s=0.02), laplace_sweep(lattice=19, tau=0.8), laplace_sweep(lattice=19, tau=1.2)]
+    elif what == "viscosity":
+        out = [viscosity_sweep(lattice=q) for q in (19, 27)]
     elif what == "e3":
         out = [local_error_curves(ncomp=2), local_error_curves(ncomp=1)]
     else:
-        raise SystemExit("usage: python -m paper_2301_01622_gb300.experiments outcome|laplace|e3")
+        raise SystemExit("usage: python -m paper_2301_01622_gb300.experiments outcome|laplace|viscosity|e3")
     print(json.dumps(out))
 
 

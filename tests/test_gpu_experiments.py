@@ -132,3 +132,12 @@ def test_config_size_collision_outcome(A_h, expect):
     rec = ex.droplet_outcome(A_h, steps=20000, diag_every=2000, count_every=20000)
     assert rec["final_count"] == expect
     assert abs(rec["mass1"][-1] - rec["mass1"][0]) < 1e-3 * rec["mass1"][0]
+
+
+def test_mixture_viscosity():
+    """Shear wave in a uniform mixture (no interface), FP64, D3Q19 and D3Q27:
+    the decay gives nu = cs^2 (tau - 1/2) within 1 % for tau = 0.6 .. 1.5."""
+    for q in (19, 27):
+        rec = ex.viscosity_sweep(lattice=q)
+        for r in rec["rows"]:
+            assert abs(r["rel_err"]) < 0.01, (q, r)

@@ -78,12 +78,15 @@ def test_tile_variant_64x4_fp64(q):
 APART = ((48, 24, 20), 5.0, 10.0, 0.02, 2.0)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3], ids=["32x8-fast", "64x4", "32x8", "32x16"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5],
+                         ids=["32x8-fast-rolled", "64x4", "32x8", "32x16", "32x8-fast", "64x4-fast-rolled"])
 @pytest.mark.parametrize("q", [19, 27])
 def test_tile_variants_fp32(q, variant):
     """Every FP32 variant of the two-component kernel (tile 32 x 8 with
-    approximate FP32 quotients for phi, 1/rho and 1/|G| -- the default --,
-    and 64 x 4, 32 x 8, 32 x 16 with IEEE quotients)
+    approximate FP32 quotients for phi, 1/rho and 1/|G| and a rolled plane
+    loop -- the default --, 64 x 4, 32 x 8, 32 x 16 with IEEE quotients, 32 x 8
+    with approximate quotients and the unrolled loop, 64 x 4 with approximate
+    quotients and the rolled loop)
     computes the same step: approaching off-axis pair, 100 steps, within
     1e-5 of the FP64 oracle per shifted field."""
     shape, radius, gap, speed, impact = APART
