@@ -334,6 +334,20 @@ LLB_API int llb_batch_step_graph(llb_batch* b, int nsteps);
  * fastest, report it through *variant (may be NULL).  Synchronises. */
 LLB_API int llb_batch_autotune(llb_batch* b, int trials, int* variant);
 
+/* Bounds checks (library built with -DLLB_CHECKED, libllb_checked.so).
+ * In that build every shared- and global-memory index of the stencil kernels
+ * (moment-only one- and two-component, direct, TMA, batch, population) is
+ * compared with its buffer's extent before the access; an access out of range
+ * is skipped and the first one is recorded with a site code (1 exchange
+ * write, 2 exchange read, 3 state load, 4 state store, 5 ghost store, 6 TMA
+ * stage read, 7 phase-field read/write, 8 near-contact probe, 9 population
+ * array).  This call synchronises the device, sets *enabled to 1 in the
+ * checked build (0 in the normal one, where *site and *index are always 0),
+ * and returns and clears the first record of each kernel file: *site = 0 when
+ * nothing was out of range, else the site and the offending index.  Any
+ * argument may be NULL.  Returns LLB_OK or LLB_ECUDA. */
+LLB_API int llb_checked_status(int* enabled, int* site, long long* index);
+
 /* Static strings; never NULL. */
 LLB_API const char* llb_status_string(int status);
 LLB_API const char* llb_last_error(const llb_ctx* ctx);

@@ -3,6 +3,11 @@
 Each translation unit under ``csrc/`` is compiled in parallel into
 ``_build/`` and linked into ``libllb.so`` next to this file.  No cmake, no
 torch extension machinery: the library is a plain C-ABI shared object.
+
+``build(checked=True)`` compiles the same sources with ``-DLLB_CHECKED`` into
+``_build_checked/`` and ``libllb_checked.so``: every stencil-kernel index is
+compared with its buffer's extent and an out-of-range access is skipped and
+recorded (``llb_checked_status``) instead of touching memory.
 """
 from __future__ import annotations
 
@@ -16,6 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libllb.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libllb_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -47,8 +54,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, bdir: str) -> str:
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _headers()):
         cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,27 +64,49 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=None, force: bool = False) -> str:
-    """Compile and link libllb.so; returns its path.  Incremental unless force."""
+def build(verbose: bool = False, extra=None, force: bool = False, checked: bool = False,
+          pool: cf.Executor | None = None) -> str:
+    """Compile and link libllb.so (libllb_checked.so if checked); returns its
+    path.  Incremental unless force."""
     extra = list(extra or [])
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if checked:
+        extra.append("-DLLB_CHECKED")
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    own = pool is None
+    ex = pool or cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4))
+    try:
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
+    finally:
+        if own:
+            ex.shutdown()
+    if force or _stale(lib, objs):
+        tmp = lib + ".tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}", file=sys.stderr)
-    return LIB
+        print(f"built {lib}", file=sys.stderr)
+    return lib
+
+
+def build_all(verbose: bool = False, force: bool = False):
+    """Both libraries, their translation units compiled by one pool."""
+    n = 2 * len(sources())
+    with cf.ThreadPoolExecutor(max_workers=min(n, os.cpu_count() or 4)) as ex:
+        futs = [cf.ThreadPoolExecutor(max_workers=1).submit(build, verbose, None, force, chk, ex)
+                for chk in (False, True)]
+        return [f.result() for f in futs]
 
 
 if __name__ == "__main__":
-    build(verbose=True, force="--force" in sys.argv)
+    if "--checked" in sys.argv:
+        build(verbose=True, force="--force" in sys.argv, checked=True)
+    else:
+        build(verbose=True, force="--force" in sys.argv)

@@ -587,4 +587,36 @@ const char* llb_last_error(const llb_ctx* c) {
     return c->msg.c_str();
 }
 
+int llb_checked_status(int* enabled, int* site, long long* index) {
+#ifdef LLB_CHECKED
+    const int on = 1;
+#else
+    const int on = 0;
+#endif
+    if (enabled) *enabled = on;
+    if (site) *site = 0;
+    if (index) *index = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return LLB_ECUDA;
+    int (*const take[])(int*, long long*) = {llb::chk_take_tiled_f32, llb::chk_take_tiled_f64,
+                                             llb::chk_take_tiled_f16, llb::chk_take_tiled_bf16,
+                                             llb::chk_take_step,      llb::chk_take_tma,
+                                             llb::chk_take_cg,        llb::chk_take_cg_batch,
+                                             llb::chk_take_pop};
+    int first = 0;
+    long long first_i = 0;
+    bool failed = false;
+    for (auto f : take) {
+        int s = 0;
+        long long i = 0;
+        if (f(&s, &i) != 0) failed = true;
+        if (s && !first) {
+            first = s;
+            first_i = i;
+        }
+    }
+    if (site) *site = first;
+    if (index) *index = first_i;
+    return failed ? LLB_ECUDA : LLB_OK;
+}
+
 }  // extern "C"

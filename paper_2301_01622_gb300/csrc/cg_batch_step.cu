@@ -45,4 +45,6 @@ cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, in
     LLB_CG(cg_batch_run_v, c, doms, ndom, total, grid)
 }
 
+LLB_CHK_TU(cg_batch)
+
 }  // namespace llb

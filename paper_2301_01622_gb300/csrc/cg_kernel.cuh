@@ -32,6 +32,7 @@
 
 #include <algorithm>
 
+#include "checked.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
@@ -62,7 +63,8 @@ __device__ __forceinline__ int pmod2(int v, int n) {
 
 template <class T>
 __device__ __forceinline__ Node2<T> load_node2(const T* __restrict__ p, size_t i, size_t fs) {
-    Node2<T> a;
+    Node2<T> a{};
+    if (!LLB_IN(i, fs, kChkLoad)) return a;
     a.r1 = __ldg(p + i);
     a.m.d = __ldg(p + fs + i);
     a.m.jx = __ldg(p + 2 * fs + i);
@@ -83,6 +85,7 @@ __device__ __forceinline__ void store_node2(T* __restrict__ p, const Layout& L, 
     for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
         const size_t i = L.at(gx, gy, z);
         const size_t fs = L.fs;
+        if (!LLB_IN(i, fs, kChkGhost)) return;
         p[i] = r1;
         p[fs + i] = m.d;
         p[2 * fs + i] = m.jx;
@@ -222,12 +225,14 @@ __device__ __forceinline__ Src2<T> cg_collide(const Node2<T>& a, T Gx, T Gy, T G
 // the z-marching kernel.  Pm, P0, Pp: phi of planes s-1, s, s+1 in shared
 // memory; b = index of the node in a phi plane; the probes read phi from the
 // moments in global memory (L2).
-template <class L, class T, int HX2, bool FAST>
+template <class L, class T, int HX2, int HN2, bool FAST>
 __device__ __forceinline__ Src2<T> collide2(const Node2<T>& a, const T* __restrict__ Pm, const T* __restrict__ P0,
                                             const T* __restrict__ Pp, int b, const CGPar<T>& p,
                                             const T* __restrict__ in, const Layout& lay, int gx, int gy, int gz) {
     // isotropic gradient: sum over opposite pairs of w c (phi(+c) - phi(-c)) / cs^2
     T Gx = T(0), Gy = T(0), Gz = T(0);
+    // every neighbour slot b +- (cy HX2 + cx) lies between these two
+    const bool in_ring = LLB_IN(b - HX2 - 1, HN2, kChkPhi) && LLB_IN(b + HX2 + 1, HN2, kChkPhi);
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
@@ -238,6 +243,7 @@ __device__ __forceinline__ Src2<T> collide2(const Node2<T>& a, const T* __restri
                 if (!lead || !L::has(cx, cy, cz)) continue;
                 const T* Pf = cz > 0 ? Pp : (cz < 0 ? Pm : P0);
                 const T* Pb = cz > 0 ? Pm : (cz < 0 ? Pp : P0);
+                if (!in_ring) continue;
                 const T diff = Pf[b + cy * HX2 + cx] - Pb[b - cy * HX2 - cx];
                 const T wd = T(3.0 * L::w(cx, cy, cz)) * diff;
                 if (cx) Gx += T(cx) * wd;
@@ -246,6 +252,7 @@ __device__ __forceinline__ Src2<T> collide2(const Node2<T>& a, const T* __restri
             }
     return cg_collide<T, FAST>(a, Gx, Gy, Gz, P0[b], p, [&](int ox, int oy, int oz) {
         const size_t q = lay.at(pmod2(gx + ox, lay.nx), pmod2(gy + oy, lay.ny), pmod2(gz + oz, lay.nz));
+        if (!LLB_IN(q, lay.fs, kChkProbe)) return T(0);
         return phi_of<false>(__ldg(in + q), __ldg(in + lay.fs + q));
     });
 }
@@ -260,6 +267,7 @@ __host__ __device__ constexpr bool wanted2(int cx, int cy) {
 // with e_c = e w (c.n) / |c|.
 template <class L, class T, int HN, int RX = 2, int RY = 2>
 __device__ __forceinline__ void publish2(GH<T>* __restrict__ X, int n, const Src2<T>& s) {
+    if (!LLB_IN(n, HN, kChkPublish)) return;
     const Mom<T>& c = s.c;
     const T s0 = g_shared(c);
 #pragma unroll
@@ -297,6 +305,7 @@ __device__ __forceinline__ void publish2(GH<T>* __restrict__ X, int n, const Src
 // along which it feeds the tile.  One code path for both signs.
 template <class L, class T, int HN>
 __device__ __forceinline__ void publish2_side(GH<T>* __restrict__ X, int n, const Src2<T>& s, int sx) {
+    if (!LLB_IN(n, HN, kChkPublish)) return;
     const Mom<T>& c = s.c;
     const T sg = T(sx);
     const T base = g_shared(c) + T(4.5) * c.axx;
@@ -343,6 +352,8 @@ __device__ __forceinline__ void acc2_to(T& a, T v) {
 // plane and add them into the accumulator of plane s + CZ (INIT: assigned).
 template <class L, class T, int CZ, int HN, int HX, bool INIT = false>
 __device__ __forceinline__ void add_plane2(const GH<T>* __restrict__ X, int n, T g_own, T h_own, Acc2<T>& A) {
+    // every neighbour slot n - cy HX - cx lies between these two
+    if (!LLB_IN(n - HX - 1, HN, kChkGather) || !LLB_IN(n + HX + 1, HN, kChkGather)) return;
 #define LLB_GH(cx, cy) X[kslot2<L>(cx, cy, CZ) * HN + n - (cy) * HX - (cx)]
     static_assert(L::has(1, 0, CZ) && L::has(0, 1, CZ), "lattice without the axis-plane directions");
     const GH<T> ax = LLB_GH(1, 0), bx = LLB_GH(-1, 0), ay = LLB_GH(0, 1), by = LLB_GH(0, -1);
@@ -467,7 +478,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
         const size_t zo = (size_t)pmod2(za - 2 + pz, nz) * plane;
 #pragma unroll
         for (int q = 0; q < NJ; ++q)
-            if (t + q * NT < HN2)
+            if (t + q * NT < HN2 && LLB_IN(zo + offj[q], fs, kChkLoad))
                 PH[pz * HN2 + t + q * NT] = phi_of<FAST>(__ldg(in + zo + offj[q]), __ldg(in + fs + zo + offj[q]));
     }
     // registers: phi inputs of plane za+1, moments of source plane za-1
@@ -478,7 +489,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
         for (int q = 0; q < NJ; ++q) {
             pr1[q] = T(0);
             pd[q] = T(0);
-            if (t + q * NT < HN2) {
+            if (t + q * NT < HN2 && LLB_IN(zo + offj[q], fs, kChkLoad)) {
                 pr1[q] = __ldg(in + zo + offj[q]);
                 pd[q] = __ldg(in + fs + zo + offj[q]);
             }
@@ -517,7 +528,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
         const T* Pm = PH + sm * HN2;
         const T* P0 = PH + s0i * HN2;
         const T* Pp = PH + sp * HN2;
-        const Src2<T> c1 = collide2<L, T, HX2, FAST>(m1, Pm, P0, Pp, b1, prm, in, lay, gx1, gy1, zs);
+        const Src2<T> c1 = collide2<L, T, HX2, HN2, FAST>(m1, Pm, P0, Pp, b1, prm, in, lay, gx1, gy1, zs);
         if (more) m1 = load_node2(in, (size_t)z1 * plane + off1, fs);
         publish2<L, T, HN1>(XG, n1, c1);
         // own column (c_x = c_y = 0)
@@ -529,7 +540,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
         const T hb = c1.r1 * (wz + wq), ho = c1.r1 * wl + ez;
         const T h_p = hb + ho, h_m = hb - ho, h_0 = c1.r1 * (w0 + g_0);
         if (role2) {
-            const Src2<T> c2 = collide2<L, T, HX2, FAST>(m2, Pm, P0, Pp, b2, prm, in, lay, gx2, gy2, zs);
+            const Src2<T> c2 = collide2<L, T, HX2, HN2, FAST>(m2, Pm, P0, Pp, b2, prm, in, lay, gx2, gy2, zs);
             if (more) m2 = load_node2(in, (size_t)z1 * plane + off2, fs);
             if (role2 == 1) publish2<L, T, HN1, 2, 1>(XG, n2, c2);
             else if (role2 == 2) publish2<L, T, HN1, 2, -1>(XG, n2, c2);
@@ -544,7 +555,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
                 const size_t zq = (size_t)z3 * plane;
 #pragma unroll
                 for (int q = 0; q < NJ; ++q)
-                    if (t + q * NT < HN2) {
+                    if (t + q * NT < HN2 && LLB_IN(zq + offj[q], fs, kChkLoad)) {
                         pr1[q] = __ldg(in + zq + offj[q]);
                         pd[q] = __ldg(in + fs + zq + offj[q]);
                     }
@@ -555,7 +566,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
         add_plane2<L, T, 1, HN1, HX1, true>(XG, n1, g_p, h_p, Z);
         if (s - 1 >= za && store_ok) {
             const Mom<T> r = X.a.finish();
-            store_node2_at(out1, fs, X.r1, r);
+            if (LLB_IN(out1 - out, fs, kChkStore)) store_node2_at(out1, fs, X.r1, r);
             if (ghost) store_node2(out, lay, ox, oy, s - 1, X.r1, r);
             out1 += plane;
         }

@@ -36,4 +36,6 @@ cudaError_t cg_run_v(const llb_ctx& c, const void* in, void* out) {
 int cg_tiled_ctas(const llb_ctx& c) { LLB_CG(cg_ctas_v, c) }
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out) { LLB_CG(cg_run_v, c, in, out) }
 
+LLB_CHK_TU(cg)
+
 }  // namespace llb

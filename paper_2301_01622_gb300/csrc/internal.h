@@ -120,6 +120,18 @@ int cg_batch_ctas(const llb_ctx& c);
 void cg_batch_plan(const llb_ctx& c, int grid, BatchDom* d);
 cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid);
 
+// Bounds-check records of the kernel translation units (checked build; the
+// normal build reports none).  Read and clear; -1 if the copy fails.
+int chk_take_tiled_f32(int* site, long long* index);
+int chk_take_tiled_f64(int* site, long long* index);
+int chk_take_tiled_f16(int* site, long long* index);
+int chk_take_tiled_bf16(int* site, long long* index);
+int chk_take_step(int* site, long long* index);
+int chk_take_tma(int* site, long long* index);
+int chk_take_cg(int* site, long long* index);
+int chk_take_cg_batch(int* site, long long* index);
+int chk_take_pop(int* site, long long* index);
+
 // Population-storing baselines (population_step.cu)
 cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);
 // state <- populations reconstructed from shifted moments (un-streamed so a pull reads them)

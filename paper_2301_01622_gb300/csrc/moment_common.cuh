@@ -14,6 +14,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "checked.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
@@ -61,7 +62,10 @@ __device__ __forceinline__ void store_mom(S* __restrict__ p, size_t idx, size_t 
 // Store node (x, y, z) and its periodic ghost copies.
 template <class T, class S>
 __device__ __forceinline__ void store_node(S* __restrict__ p, const Layout& L, int x, int y, int z, const Mom<T>& m) {
-    for_node_and_ghosts(L, x, y, [&](int gx, int gy) { store_mom(p, L.at(gx, gy, z), L.fs, m); });
+    for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
+        const size_t i = L.at(gx, gy, z);
+        if (LLB_IN(i, L.fs, kChkGhost)) store_mom(p, i, L.fs, m);
+    });
 }
 
 __host__ __device__ __forceinline__ int pmod(int v, int n) {
@@ -144,6 +148,7 @@ __host__ __device__ constexpr bool wanted(int cx, int cy) {
 // l = 3 c.j.
 template <class L, class T, int HN, int RX = kAny, int RY = kAny>
 __device__ __forceinline__ void publish(T* __restrict__ G, int n, const Mom<T>& c) {
+    if (!LLB_IN(n, HN, kChkPublish)) return;
     const T s0 = g_shared(c);
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
@@ -181,6 +186,7 @@ __device__ __forceinline__ void publish(T* __restrict__ G, int n, const Mom<T>& 
 // not diverge.
 template <class L, class T, int HN>
 __device__ __forceinline__ void publish_side(T* __restrict__ G, int n, const Mom<T>& c, int sx) {
+    if (!LLB_IN(n, HN, kChkPublish)) return;
     const T s = T(sx);
     const T base = g_shared(c) + T(4.5) * c.axx;
     const T sxy = s * c.axy, sxz = s * c.axz, sjx = T(3) * s * c.jx;
@@ -276,6 +282,8 @@ template <class L, class T, int HN, int HX>
 __device__ __forceinline__ void gather(const T* __restrict__ G, int n1, T g_m, T g_0, T g_p, Acc<T>& X, Acc<T>& Y,
                                        Acc<T>& Z) {
     constexpr int NS = n_xy_shifted<L>();
+    // every neighbour slot n1 - cy HX - cx lies between these two
+    if (!LLB_IN(n1 - HX - 1, HN, kChkGather) || !LLB_IN(n1 + HX + 1, HN, kChkGather)) return;
     T g[NS];
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(128) k_moment_direct(const S* __restrict__ in,
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
                 const size_t s = lay.at(wrap_idx(x - cx, lay.nx), wrap_idx(y - cy, lay.ny), wrap_idx(z - cz, lay.nz));
+                if (!LLB_IN(s, lay.fs, kChkLoad)) continue;
                 const Mom<T> c = collide(load_mom<T>(in, s, lay.fs), omega);
                 acc.add(g_dir<L, T>(c, g_shared(c), cx, cy, cz), cx, cy, cz);
             }
@@ -99,5 +100,7 @@ bool moment_tiled_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
     }
     return encode_box_map(c, buf, w, h, out);
 }
+
+LLB_CHK_TU(step)
 
 }  // namespace llb

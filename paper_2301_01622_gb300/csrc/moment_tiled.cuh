@@ -135,16 +135,17 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         // source plane of the next load, wrapped incrementally (no division per plane)
         int zn = pmod(za - 1, nz);
         size_t zn_off = (size_t)zn * plane;
-        Mom<T> m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
-        Mom<T> m2;
-        if (has2) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
+        const long long o1 = in1 - in, o2 = in2 - in;  // node offsets within a field (plane 0)
+        Mom<T> m1{}, m2{};
+        if (LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
+        if (has2 && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
 
         auto put = [&](const Acc<T>& A, int z) {
             const Mom<T> r = A.finish();
-            store_mom(out1, 0, lay.fs, r);
+            if (LLB_IN(out1 - out, lay.fs, kChkStore)) store_mom(out1, 0, lay.fs, r);
             if (ghost) store_node(out, lay, ox, oy, z, r);
             out1 += plane;
         };
@@ -169,13 +170,13 @@ __global__ void __launch_bounds__(BX * BY, MINB)
                 }
             }
             const Mom<T> c1 = collide<T, FAST>(m1, omega);
-            if (more) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
+            if (more && LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
             publish<L, T, HN>(G, n1, c1);
             T g_m, g_0, g_p;
             own_column<L, T>(c1, g_m, g_0, g_p);
             if (has2) {
                 const Mom<T> c2 = collide<T, FAST>(m2, omega);
-                if (more) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
+                if (more && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
                 publish_halo<L, T, HN>(G, n2, role2, sx2, c2);
             }
             if constexpr (SPLIT) {
@@ -327,4 +328,5 @@ void tiled_box(int* w, int* h) {
     void moment_tiled_box_##SUFFIX(const llb_ctx& c, int* w, int* h) {                                         \
         if (c.Q == 19) box_l<D3Q19>(c, w, h); else box_l<D3Q27>(c, w, h);                                      \
     }                                                                                                          \
+    LLB_CHK_TU(tiled_##SUFFIX)                                                                                 \
     }

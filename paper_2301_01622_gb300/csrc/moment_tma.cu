@@ -46,8 +46,9 @@ struct TmaCfg {
 
 template <class T, int SF, int SW>
 __device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int hy) {
+    Mom<T> m{};
+    if (!LLB_IN(hy * SW + hx + 3, SF, kChkStage)) return m;
     const T* p = S + hy * SW + hx + 3;
-    Mom<T> m;
     m.d = p[0];
     m.jx = p[SF];
     m.jy = p[2 * SF];
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
             if (s - 1 >= za && store_ok) {
                 const Mom<T> r = X.finish();
-                store_mom(out1, 0, lay.fs, r);
+                if (LLB_IN(out1 - out, lay.fs, kChkStore)) store_mom(out1, 0, lay.fs, r);
                 if (ghost) store_node(out, lay, ox, oy, s - 1, r);
                 out1 += plane;
             }
@@ -291,5 +292,7 @@ cudaError_t launch_moment_tma(const llb_ctx& c, int in_index, void* out) {
 bool moment_tma_encode(const llb_ctx& c, void* buf, CUtensorMap* out) {
     LLB_MDISPATCH(tma_encode, false, c, buf, out)
 }
+
+LLB_CHK_TU(tma)
 
 }  // namespace llb

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_pop_step(const T* __restrict__ in, T* _
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
-    const size_t idx = ((size_t)z * ny + y) * nx + x;
+    const size_t idx = LLB_CLAMP(((size_t)z * ny + y) * nx + x, N, kChkPop);
     T g[L::Q];
     Acc<T> acc;
     acc.zero();
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128) k_pop_step(const T* __restrict__ in, T* _
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx);
+                const size_t s = LLB_CLAMP(((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx), N, kChkPop);
                 g[k] = in[(size_t)k * N + s];
                 acc.add(g[k], cx, cy, cz);
                 ++k;
@@ -98,7 +98,7 @@ __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
-    const size_t idx = ((size_t)z * ny + y) * nx + x;
+    const size_t idx = LLB_CLAMP(((size_t)z * ny + y) * nx + x, N, kChkPop);
     int k = 0;
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
@@ -107,7 +107,7 @@ __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz));
+                const size_t s = LLB_CLAMP(lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz)), lay.fs, kChkLoad);
                 const Mom<T> m = load_mom(mom, s, lay.fs);
                 st[(size_t)k * N + idx] = g_dir<L, T>(m, g_shared(m), cx, cy, cz);
                 ++k;
@@ -130,11 +130,11 @@ __global__ void k_moments_from_pop(const T* __restrict__ st, T* __restrict__ mom
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx);
+                const size_t s = LLB_CLAMP(((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx), N, kChkPop);
                 acc.add(st[(size_t)k * N + s], cx, cy, cz);
                 ++k;
             }
-    store_mom(mom, lay.at(x, y, z), lay.fs, acc.finish());
+    store_mom(mom, LLB_CLAMP(lay.at(x, y, z), lay.fs, kChkStore), lay.fs, acc.finish());
 }
 
 // ---------------------------------------------------------------------------
@@ -156,12 +156,12 @@ __global__ void __launch_bounds__(128) k_pop2_phase(const T* __restrict__ in, T*
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx);
+                const size_t s = LLB_CLAMP(((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx), N, kChkPop);
                 d += in[(size_t)k * N + s];
                 r1 += in[(size_t)(L::Q + k) * N + s];
                 ++k;
             }
-    phi[((size_t)z * ny + y) * nx + x] = T(2) * r1 / (T(1) + d) - T(1);
+    phi[LLB_CLAMP(((size_t)z * ny + y) * nx + x, N, kChkPhi)] = T(2) * r1 / (T(1) + d) - T(1);
 }
 
 template <class L, class T, bool BGK>
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(128) k_pop2_step(const T* __restrict__ in, T* 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
-    const size_t idx = ((size_t)z * ny + y) * nx + x;
+    const size_t idx = LLB_CLAMP(((size_t)z * ny + y) * nx + x, N, kChkPop);
     T g[L::Q];
     Acc<T> acc;
     acc.zero();
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(128) k_pop2_step(const T* __restrict__ in, T* 
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx);
+                const size_t s = LLB_CLAMP(((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx), N, kChkPop);
                 g[k] = in[(size_t)k * N + s];
                 r1 += in[(size_t)(L::Q + k) * N + s];
                 acc.add(g[k], cx, cy, cz);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) k_pop2_step(const T* __restrict__ in, T* 
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0 && cz == 0)) continue;
-                const T v = phi[((size_t)wrap_idx(z + cz, nz) * ny + wrap_idx(y + cy, ny)) * nx + wrap_idx(x + cx, nx)];
+                const T v = phi[LLB_CLAMP(((size_t)wrap_idx(z + cz, nz) * ny + wrap_idx(y + cy, ny)) * nx + wrap_idx(x + cx, nx), N, kChkPhi)];
                 const T wv = T(3.0 * L::w(cx, cy, cz)) * v;
                 if (cx) Gx += T(cx) * wv;
                 if (cy) Gy += T(cy) * wv;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_pop2_step(const T* __restrict__ in, T* 
             }
     const cg::Src2<T> s = cg::cg_collide<T, false>(a, Gx, Gy, Gz, phi[idx], prm, [&](int ox, int oy, int oz) {
         const int px = cg::pmod2(x + ox, nx), py = cg::pmod2(y + oy, ny), pz = cg::pmod2(z + oz, nz);
-        return phi[((size_t)pz * ny + py) * nx + px];
+        return phi[LLB_CLAMP(((size_t)pz * ny + py) * nx + px, N, kChkProbe)];
     });
     const T s0c = g_shared(s.c), s0m = g_shared(a.m);
     const T one_m = T(1) - prm.omega;
@@ -244,7 +244,7 @@ __global__ void k_pop2_from_moments(const T* __restrict__ mom, T* __restrict__ s
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
-    const size_t idx = ((size_t)z * ny + y) * nx + x;
+    const size_t idx = LLB_CLAMP(((size_t)z * ny + y) * nx + x, N, kChkPop);
     int k = 0;
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
@@ -253,7 +253,7 @@ __global__ void k_pop2_from_moments(const T* __restrict__ mom, T* __restrict__ s
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz));
+                const size_t s = LLB_CLAMP(lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz)), lay.fs, kChkLoad);
                 const T r1 = mom[s];
                 const Mom<T> m = load_mom(mom + lay.fs, s, lay.fs);
                 const T gr = g_dir<L, T>(m, g_shared(m), cx, cy, cz);
@@ -280,12 +280,12 @@ __global__ void k_moments2_from_pop(const T* __restrict__ st, T* __restrict__ mo
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
-                const size_t s = ((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx);
+                const size_t s = LLB_CLAMP(((size_t)wrap_idx(z - cz, nz) * ny + wrap_idx(y - cy, ny)) * nx + wrap_idx(x - cx, nx), N, kChkPop);
                 acc.add(st[(size_t)k * N + s], cx, cy, cz);
                 r1 += st[(size_t)(L::Q + k) * N + s];
                 ++k;
             }
-    const size_t i = lay.at(x, y, z);
+    const size_t i = LLB_CLAMP(lay.at(x, y, z), lay.fs, kChkStore);
     mom[i] = r1;
     store_mom(mom + lay.fs, i, lay.fs, acc.finish());
 }
@@ -372,5 +372,7 @@ cudaError_t launch_population_from_moments(const llb_ctx& c, const void* mom, vo
 cudaError_t launch_moments_from_population(const llb_ctx& c, const void* state, void* mom) {
     return LLB_DISPATCH(to_mom_t, c, state, mom);
 }
+
+LLB_CHK_TU(pop)
 
 }  // namespace llb

@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libllb.so")
+# LLB_CHECKED=1 loads the bounds-checked build (libllb_checked.so) instead
+LIB_PATH = os.path.join(HERE, "libllb_checked.so" if os.environ.get("LLB_CHECKED") == "1" else "libllb.so")
 
 LLB_OK, LLB_EINVAL, LLB_ENOMEM, LLB_ECUDA, LLB_EUNSTABLE, LLB_ETIMEOUT, LLB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LLB_F64, LLB_F32, LLB_F16S, LLB_BF16S = 0, 1, 2, 3
@@ -91,6 +92,7 @@ _SIGS = {
     "llb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "llb_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                               C.POINTER(C.c_double)]),
+    "llb_checked_status": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "llb_status_string": (C.c_char_p, [C.c_int]),
     "llb_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -101,7 +103,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libllb.so not found at {LIB_PATH}; build it first "
+            raise RuntimeError(f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}; build it first "
                                "(python -c 'import __graft_entry__ as g; g.build()')")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
@@ -280,6 +282,14 @@ def llb_diagnostics_noalloc(dev_m, nx, ny, nz, stream=None) -> dict:
 
 def llb_synchronize(ctx):
     _check(lib().llb_synchronize(ctx), "llb_synchronize", ctx)
+
+
+def llb_checked_status():
+    """(enabled, site, index): the first out-of-range access recorded by the
+    bounds-checked build since the last call (site 0: none).  Synchronises."""
+    en, site, idx = C.c_int(0), C.c_int(0), C.c_longlong(0)
+    _check(lib().llb_checked_status(C.byref(en), C.byref(site), C.byref(idx)), "llb_checked_status")
+    return en.value, site.value, idx.value
 
 
 def llb_steps_done(ctx) -> int:

@@ -94,3 +94,23 @@ def test_null_context_calls_fail_cleanly():
     assert L.llb_synchronize(None) == llb.LLB_EINVAL
     L.llb_destroy(None)  # NULL-safe
     assert llb.status_string(llb.LLB_EUNSTABLE).startswith("unstable")
+
+
+def test_checked_build_exports_the_same_symbols_and_reports_itself():
+    """libllb_checked.so (built with -DLLB_CHECKED) exports every declared
+    function; llb_checked_status reports enabled = 1 there and 0 in libllb.so
+    (*enabled is set before the device synchronisation, so no GPU is needed)."""
+    import ctypes as C
+
+    from paper_2301_01622_gb300 import build as B
+    if not (os.path.exists(B.LIB) and os.path.exists(B.LIB_CHECKED)):
+        pytest.skip("libraries not built")
+    for path, want in ((B.LIB, 0), (B.LIB_CHECKED, 1)):
+        L = C.CDLL(path)
+        for n in _declared():
+            assert hasattr(L, n), f"{n} not exported by {os.path.basename(path)}"
+        en, site, idx = C.c_int(-1), C.c_int(-1), C.c_longlong(-1)
+        L.llb_checked_status.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+        L.llb_checked_status(C.byref(en), C.byref(site), C.byref(idx))
+        assert en.value == want
+        assert site.value == 0 and idx.value == 0
