@@ -1,16 +1,18 @@
 // llb_step_host: moments in from host memory, time steps, moments out to host
 // memory, with the host<->device copies overlapped with the device work.
 //
-// The box is cut into K slabs of whole z-planes.  Three streams of the
-// context carry the work: the copy-in stream copies slab k of the canonical
-// input (one copy per field) and converts it to the shifted state; the step
-// stream runs the step for the output planes of slab k as soon as the input
-// slabs k-1, k, k+1 have arrived (the pull reaches one plane across each
-// slab boundary); the copy-out stream converts the finished output planes of
-// slab k back to canonical moments and copies them to the host.  Events
-// order the three streams; slab copies in, steps and copies out of
-// different slabs run at the same time, so the call takes about as long as
-// the larger of the two host copies.  Slabs are stepped in the order
+// The box is cut into K slabs of whole z-planes (up to 32, at least 8 planes
+// each).  Three streams of the context carry the work:
+//   * copy-in: one 2D copy per slab (the ten fields of the slab, each a
+//     contiguous run, strided by the field size) into a device staging buffer;
+//   * step: converts each arrived slab to the shifted state, runs the step for
+//     the output planes of slab k as soon as the input slabs k-1, k, k+1 are
+//     converted (the pull reaches one plane across each slab boundary), and
+//     converts the finished output planes back to canonical moments;
+//   * copy-out: one 2D copy per finished slab to the host.
+// The copy streams carry nothing but copies, so both directions of the host
+// link stay busy; the conversions and steps (tens of microseconds per slab)
+// run between them.  Events order the streams.  Slabs are stepped in the order
 // 1, 2, ..., K-1, 0: slab 0 needs the last slab of the box (periodic wrap).
 //
 // With nsteps > 1 the first step is pipelined with the copies in, the middle
@@ -26,7 +28,7 @@
 namespace llb {
 namespace {
 
-constexpr int kMaxSlabs = 16;
+constexpr int kMaxSlabs = 32;
 
 int pipe_setup(llb_ctx* c, size_t out_bytes) {
     for (int k = 0; k < 3; ++k)
@@ -51,8 +53,29 @@ int pipe_setup(llb_ctx* c, size_t out_bytes) {
     return LLB_OK;
 }
 
+// Copy the ten fields of planes [z0, z1) between host and device canonical
+// arrays (field-major, field size N elements of es bytes): one 2D copy when
+// the field stride is within the copy engine's pitch limit, else one copy per
+// field.
+cudaError_t copy_slab(void* dst, const void* src, size_t N, size_t es, size_t off, size_t len, cudaMemcpyKind kind,
+                      cudaStream_t st) {
+    static int max_pitch = -1;
+    if (max_pitch < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxPitch, dev) != cudaSuccess)
+            v = 0;
+        max_pitch = v;
+    }
+    char* d = static_cast<char*>(dst) + off;
+    const char* s = static_cast<const char*>(src) + off;
+    if (N * es <= (size_t)max_pitch) return cudaMemcpy2DAsync(d, N * es, s, N * es, len, 10, kind, st);
+    for (int f = 0; f < 10; ++f)
+        if (cudaError_t e = cudaMemcpyAsync(d + f * N * es, s + f * N * es, len, kind, st); e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 struct Events {
-    cudaEvent_t ev[3 * kMaxSlabs + 2] = {};
+    cudaEvent_t ev[2 * kMaxSlabs + 1] = {};
     int n = 0;
     ~Events() {
         for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
@@ -107,14 +130,11 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
     int zb[kMaxSlabs + 1];
     for (int k = 0; k <= K; ++k) zb[k] = (int)((long long)k * c->nz / K);
     Events E;
-    cudaError_t e = E.make(3 * K + 2);
-    cudaEvent_t* ev_in = E.ev;             // slab k converted into the state
-    cudaEvent_t* ev_step = E.ev + K;       // output planes of slab k written
-    cudaEvent_t* ev_out = E.ev + 2 * K;    // slab k copied to the host (unused but for ordering)
-    cudaEvent_t ev_start = E.ev[3 * K], ev_mid = E.ev[3 * K + 1];
+    cudaError_t e = E.make(2 * K + 1);
+    cudaEvent_t* ev_copied = E.ev;         // slab k of the input is in the staging buffer
+    cudaEvent_t* ev_ready = E.ev + K;      // output planes of slab k are canonical in the output staging buffer
+    cudaEvent_t ev_start = E.ev[2 * K];
     cudaStream_t sin = c->pipe[0], scmp = c->pipe[1], sout = c->pipe[2];
-    const char* host_i = static_cast<const char*>(host_in);
-    char* host_o = static_cast<char*>(host_out);
     char* dev_i = static_cast<char*>(c->staging);
     char* dev_o = static_cast<char*>(c->staging_out);
     int* bad = static_cast<int*>(c->flag_dev);
@@ -122,39 +142,39 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev_start, c->stream);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(c->pipe[k], ev_start, 0);
+    auto slab_off = [&](int k) { return (size_t)zb[k] * plane * es; };
+    auto slab_len = [&](int k) { return (size_t)(zb[k + 1] - zb[k]) * plane * es; };
 
-    // copies in: slab by slab, one copy per field
+    // copies in: nothing but copies on this stream
     int cur = c->cur;
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
-        const size_t off = (size_t)zb[k] * plane * es, len = (size_t)(zb[k + 1] - zb[k]) * plane * es;
-        for (int f = 0; f < 10 && e == cudaSuccess; ++f)
-            e = cudaMemcpyAsync(dev_i + f * N * es + off, host_i + f * N * es + off, len, cudaMemcpyHostToDevice, sin);
-        if (e == cudaSuccess)
-            e = launch_canonical_to_shifted_range(*c, dev_i, host_dtype, c->buf[cur], bad, zb[k], zb[k + 1], sin);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], sin);
+        e = copy_slab(dev_i, host_in, N, es, slab_off(k), slab_len(k), cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_copied[k], sin);
     }
-    // one pipelined step (from buf[cur] to buf[1 - cur]); `wait_in`: slabs wait for their inputs,
-    // `copy_out`: finished slabs go straight to the host
+    int converted = 0;  // input slabs 0 .. converted-1 are in the shifted state
+    // one pipelined step (from buf[cur] to buf[1 - cur]); `wait_in`: input slabs are
+    // converted as they arrive, `copy_out`: finished slabs go straight to the host
     auto pipelined_step = [&](bool wait_in, bool copy_out) {
         for (int i = 0; i < K && e == cudaSuccess; ++i) {
             const int k = K == 1 ? 0 : (i + 1) % K;   // 1, 2, ..., K-1, 0
             if (wait_in) {
                 const int need = (k == K - 1 || k == 0) ? K - 1 : k + 1;  // highest input slab this slab reads
-                e = cudaStreamWaitEvent(scmp, ev_in[need], 0);
+                while (converted <= need && e == cudaSuccess) {
+                    e = cudaStreamWaitEvent(scmp, ev_copied[converted], 0);
+                    if (e == cudaSuccess)
+                        e = launch_canonical_to_shifted_range(*c, dev_i, host_dtype, c->buf[cur], bad, zb[converted],
+                                                              zb[converted + 1], scmp);
+                    ++converted;
+                }
             }
             if (e == cudaSuccess)
                 e = launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], zb[k], zb[k + 1], scmp);
-            if (e == cudaSuccess) e = cudaEventRecord(ev_step[k], scmp);
             if (copy_out && e == cudaSuccess) {
-                e = cudaStreamWaitEvent(sout, ev_step[k], 0);
+                e = launch_shifted_to_canonical_range(*c, c->buf[1 - cur], dev_o, host_dtype, zb[k], zb[k + 1], scmp);
+                if (e == cudaSuccess) e = cudaEventRecord(ev_ready[k], scmp);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_ready[k], 0);
                 if (e == cudaSuccess)
-                    e = launch_shifted_to_canonical_range(*c, c->buf[1 - cur], dev_o, host_dtype, zb[k], zb[k + 1],
-                                                          sout);
-                const size_t off = (size_t)zb[k] * plane * es, len = (size_t)(zb[k + 1] - zb[k]) * plane * es;
-                for (int f = 0; f < 10 && e == cudaSuccess; ++f)
-                    e = cudaMemcpyAsync(host_o + f * N * es + off, dev_o + f * N * es + off, len,
-                                        cudaMemcpyDeviceToHost, sout);
-                if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], sout);
+                    e = copy_slab(host_out, dev_o, N, es, slab_off(k), slab_len(k), cudaMemcpyDeviceToHost, sout);
             }
         }
         cur = 1 - cur;
@@ -166,7 +186,6 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
             e = launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], 0, c->nz, scmp);
             cur = 1 - cur;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ev_mid, scmp);
         if (e == cudaSuccess) pipelined_step(false, true);
     }
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamSynchronize(c->pipe[k]);

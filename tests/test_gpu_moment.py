@@ -349,7 +349,8 @@ def test_autotune_keeps_state(q):
 
 @pytest.mark.parametrize("nsteps", [1, 3])
 @pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64], ids=["f32", "f64"])
-@pytest.mark.parametrize("shape", [(64, 48, 40), (67, 45, 37), (33, 9, 5)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", [(64, 48, 40), (67, 45, 37), (33, 9, 5), (40, 24, 264)],
+                         ids=lambda s: "x".join(map(str, s)))
 def test_step_host_matches_sequential(shape, storage, nsteps):
     """llb_step_host (copies overlapped with per-slab steps) gives bit for bit
     what llb_init_moments + llb_step + llb_get_moments give."""
