@@ -45,6 +45,39 @@ __device__ __forceinline__ Mom<T> load_mom(const S* __restrict__ p, size_t idx, 
     return m;
 }
 
+// The ten stored elements of one node as loaded.  A kernel that loads a plane
+// ahead keeps these and converts them (from_raw) only when it collides the
+// node, so that with 16-bit storage the wait for the load falls at the use and
+// not right after the load.
+template <class S>
+struct RawMom {
+    S v[10];
+};
+
+template <class S>
+__device__ __forceinline__ RawMom<S> load_raw(const S* __restrict__ p, size_t idx, size_t fs) {
+    RawMom<S> r;
+#pragma unroll
+    for (int f = 0; f < 10; ++f) r.v[f] = __ldg(p + f * fs + idx);
+    return r;
+}
+
+template <class T, class S>
+__device__ __forceinline__ Mom<T> from_raw(const RawMom<S>& r) {
+    Mom<T> m;
+    m.d = cv_field<T>(r.v[0], 0);
+    m.jx = cv_field<T>(r.v[1], 1);
+    m.jy = cv_field<T>(r.v[2], 2);
+    m.jz = cv_field<T>(r.v[3], 3);
+    m.axx = cv_field<T>(r.v[4], 4);
+    m.ayy = cv_field<T>(r.v[5], 5);
+    m.azz = cv_field<T>(r.v[6], 6);
+    m.axy = cv_field<T>(r.v[7], 7);
+    m.axz = cv_field<T>(r.v[8], 8);
+    m.ayz = cv_field<T>(r.v[9], 9);
+    return m;
+}
+
 template <class T, class S>
 __device__ __forceinline__ void store_mom(S* __restrict__ p, size_t idx, size_t fs, const Mom<T>& m) {
     p[idx] = to_store<S>(m.d, 0);

@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         int zn = pmod(za - 1, nz);
         size_t zn_off = (size_t)zn * plane;
         const long long o1 = in1 - in, o2 = in2 - in;  // node offsets within a field (plane 0)
-        Mom<T> m1{}, m2{};
-        if (LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
-        if (has2 && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
+        RawMom<S> m1{}, m2{};  // converted at the collision
+        if (LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_raw(in1 + zn_off, 0, lay.fs);
+        if (has2 && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_raw(in2 + zn_off, 0, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
@@ -169,14 +169,14 @@ __global__ void __launch_bounds__(BX * BY, MINB)
                     zn_off += plane;
                 }
             }
-            const Mom<T> c1 = collide<T, FAST>(m1, omega);
-            if (more && LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_mom<T>(in1 + zn_off, 0, lay.fs);
+            const Mom<T> c1 = collide<T, FAST>(from_raw<T>(m1), omega);
+            if (more && LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_raw(in1 + zn_off, 0, lay.fs);
             publish<L, T, HN>(G, n1, c1);
             T g_m, g_0, g_p;
             own_column<L, T>(c1, g_m, g_0, g_p);
             if (has2) {
-                const Mom<T> c2 = collide<T, FAST>(m2, omega);
-                if (more && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_mom<T>(in2 + zn_off, 0, lay.fs);
+                const Mom<T> c2 = collide<T, FAST>(from_raw<T>(m2), omega);
+                if (more && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_raw(in2 + zn_off, 0, lay.fs);
                 publish_halo<L, T, HN>(G, n2, role2, sx2, c2);
             }
             if constexpr (SPLIT) {

@@ -25,14 +25,20 @@ struct IsNarrow<__nv_bfloat16> : std::true_type {};
 // Scale of field f (one-component order d, jx, jy, jz, Axx..Ayz) in 16-bit storage.
 __host__ __device__ constexpr float narrow_scale(int f) { return f == 0 ? 64.0f : (f < 4 ? 16.0f : 1024.0f); }
 
+// Value of field f from its stored element.
+template <class T, class S>
+__device__ __forceinline__ T cv_field(S v, int f) {
+    if constexpr (std::is_same<S, __half>::value)
+        return T(__half2float(v)) * T(1.0f / narrow_scale(f));
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+        return T(__bfloat162float(v)) * T(1.0f / narrow_scale(f));
+    else
+        return T(v);
+}
+
 template <class T, class S>
 __device__ __forceinline__ T ld_field(const S* p, int f) {
-    if constexpr (std::is_same<S, __half>::value)
-        return T(__half2float(__ldg(p))) * T(1.0f / narrow_scale(f));
-    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
-        return T(__bfloat162float(__ldg(p))) * T(1.0f / narrow_scale(f));
-    else
-        return T(__ldg(p));
+    return cv_field<T>(__ldg(p), f);
 }
 
 // Plain (non-__ldg) read, for buffers written earlier in the same kernel.
