@@ -126,10 +126,13 @@ typedef struct llb_params {
      * bound) and return; the next synchronising call reports LLB_ETIMEOUT.
      * Range 1..600000. */
     int wait_budget_ms;
-    /* Fault injection for tests; 0 in normal use.  Bit 0: every TMA stage
-     * barrier is armed for one byte more than its copy delivers, so no stage
-     * wait can complete and every wait runs out after wait_budget_ms (the
-     * copies themselves land normally; nothing faults). */
+    /* Test switches; 0 in normal use.  Bit 0 (fault injection): every TMA
+     * stage barrier is armed for one byte more than its copy delivers, so no
+     * stage wait can complete and every wait runs out after wait_budget_ms
+     * (the copies themselves land normally; nothing faults).  Bit 1: the
+     * two-component adjoint runs its first pass in the reference form, one
+     * thread per node loading its neighbours' cotangents, instead of the
+     * tiled kernel (same result up to rounding). */
     int debug_flags;
     /* Two components: 0 (default) takes the interface normal n = G/|G| only
      * where |G| >= g_min (n = 0 elsewhere).  eps > 0 takes the smooth norm

@@ -29,12 +29,15 @@
 // steps run through it in reverse (memory: ~N/K + K state copies).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "checked.cuh"
 #include "internal.h"
 #include "lattice.cuh"
 #include "layout.cuh"
+#include "moment_common.cuh"
 
 namespace llb {
 namespace {
@@ -300,6 +303,248 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_cg_phi(const T* __restr
     lam[fs + i0] -= lphi * T(2) * m[i0] * rinv * rinv;
 }
 
+// ---------------------------------------------------------------------------
+// Tiled pass 1 of the two-component adjoint (the default).  Receiver y needs,
+// for every direction c, s_c(y + c) = e_c . lam_new(y + c) and
+// t(y + c) = lam_new_rho1(y + c), and phi(y + c) for G(y).  Instead of loading
+// the 11 cotangent fields of each of its Q neighbours (k_adjoint_cg_local), a
+// persistent CTA marches a BX x BY tile through z: for each plane, every node
+// of the tile plus a one-node halo computes its Q projections once and
+// publishes them, with t and phi, into a ring of three planes in shared
+// memory; each receiver of the middle plane then reads two values per
+// direction.  Two barriers per plane (published; ring slot free again).
+template <class L, class T, int BX, int BY>
+struct AdjTile {
+    static constexpr int NT = BX * BY, HX = BX + 2, HY = BY + 2, HN = HX * HY;
+    static constexpr int NF = L::Q + 2;  // Q projections, t, phi
+    static constexpr int SLOT = NF * HN;  // elements of one plane of the ring
+    static constexpr size_t smem_bytes = 3 * (size_t)SLOT * sizeof(T);
+    static constexpr int MINB = sizeof(T) == 4 ? 3 : 1;  // CTAs per SM the register budget targets
+    static_assert(NT % 32 == 0, "whole warps");
+};
+constexpr int kAdjBX = 32, kAdjBY = 4;
+
+// Index of direction (cx, cy, cz) in the lattice, enumerated over cz, cy, cx.
+template <class L>
+__host__ __device__ constexpr int dir_index(int cx, int cy, int cz) {
+    int k = 0;
+    for (int z = -1; z <= 1; ++z)
+        for (int y = -1; y <= 1; ++y)
+            for (int x = -1; x <= 1; ++x) {
+                if (!L::has(x, y, z)) continue;
+                if (x == cx && y == cy && z == cz) return k;
+                ++k;
+            }
+    return -1;
+}
+
+// Publish node j of the tile-plus-halo region (plane index zq, wrapped) into slot S.
+template <class L, class T, int HN>
+__device__ __forceinline__ void adj_publish(const T* __restrict__ lam_new, const T* __restrict__ m, const Layout& lay,
+                                            size_t i, int j, T* __restrict__ S) {
+    const size_t fs = lay.fs;
+    if (!LLB_IN(i, fs, kChkLoad) || !LLB_IN(j, HN, kChkPublish)) return;
+    T v[11];
+#pragma unroll
+    for (int f = 0; f < 11; ++f) v[f] = lam_new[f * fs + i];
+    const T r1 = m[i], d = m[fs + i];
+    S[(L::Q + 1) * HN + j] = T(2) * r1 / (T(1) + d) - T(1);
+    S[L::Q * HN + j] = v[0];
+    // s(+-c) = even +- odd, even = v1 + (cc - cs^2 I) : vP, odd = c . vj
+    const T ev0 = v[1] - T(kCs2) * (v[5] + v[6] + v[7]);
+    S[dir_index<L>(0, 0, 0) * HN + j] = ev0;
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx) {
+                const bool lead = cx > 0 || (cx == 0 && (cy > 0 || (cy == 0 && cz > 0)));
+                if (!lead || !L::has(cx, cy, cz)) continue;
+                T ev = ev0;
+                if (cx) ev += v[5];
+                if (cy) ev += v[6];
+                if (cz) ev += v[7];
+                if (cx * cy) ev += T(cx * cy) * v[8];
+                if (cx * cz) ev += T(cx * cz) * v[9];
+                if (cy * cz) ev += T(cy * cz) * v[10];
+                T od = T(0);
+                if (cx) od += T(cx) * v[2];
+                if (cy) od += T(cy) * v[3];
+                if (cz) od += T(cz) * v[4];
+                S[dir_index<L>(cx, cy, cz) * HN + j] = ev + od;
+                S[dir_index<L>(-cx, -cy, -cz) * HN + j] = ev - od;
+            }
+}
+
+// Receiver y (node n of the region, own 11 fields in s): the direct kernel's
+// arithmetic with the neighbour quantities read from the ring planes Sm, S0, Sp
+// (planes z - 1, z, z + 1).  Writes lam(y), lam_g(y); returns y's dL/domega term.
+template <class L, class T, int HX, int HN>
+__device__ __forceinline__ double adj_receive(const T* __restrict__ Sm, const T* __restrict__ S0,
+                                              const T* __restrict__ Sp, int n, const T* s, const CGAdjPar<T>& p,
+                                              T* __restrict__ lam, T* __restrict__ lam_g, size_t i0, size_t fs) {
+    if (!LLB_IN(n - HX - 1, HN, kChkGather) || !LLB_IN(n + HX + 1, HN, kChkGather) || !LLB_IN(i0, fs, kChkStore))
+        return 0.0;
+    constexpr int Q = L::Q;
+    const T r1 = s[0], d = s[1], jx = s[2], jy = s[3], jz = s[4];
+    const T* A = s + 5;  // xx, yy, zz, xy, xz, yz
+    T G[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx) {
+                if (!L::has(cx, cy, cz) || (cx == 0 && cy == 0 && cz == 0)) continue;
+                const T* P = cz > 0 ? Sp : (cz < 0 ? Sm : S0);
+                const T wp = T(3.0 * L::w(cx, cy, cz)) * P[(Q + 1) * HN + n + cy * HX + cx];
+                G[0] += T(cx) * wp;
+                G[1] += T(cy) * wp;
+                G[2] += T(cz) * wp;
+            }
+    const T rho = T(1) + d, rinv = T(1) / rho, om = p.omega;
+    const T gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2] + p.eps2);
+    const T nv[3] = {G[0] / gn, G[1] / gn, G[2] / gn};
+    const T ks = p.A_s * gn * T(1.0 / 9.0);
+    const T jj[6] = {jx * jx, jy * jy, jz * jz, jx * jy, jx * jz, jy * jz};
+    const T nn[6] = {nv[0] * nv[0], nv[1] * nv[1], nv[2] * nv[2], nv[0] * nv[1], nv[0] * nv[2], nv[1] * nv[2]};
+    T Ap[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Ap[k] = (T(1) - om) * A[k] + om * jj[k] * rinv + ks * nn[k];
+    const T s0 = d - T(1.5) * (Ap[0] + Ap[1] + Ap[2]);
+    const T r1r = r1 * rinv;
+    const T e = p.beta * r1 * (rho - r1) * rinv;
+    T ld = T(0), lj[3] = {T(0), T(0), T(0)}, la[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T l_r1r = T(0), l_e = T(0), ln[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx) {
+                if (!L::has(cx, cy, cz)) continue;
+                const T* P = cz > 0 ? Sp : (cz < 0 ? Sm : S0);
+                const int o = n + cy * HX + cx;
+                const T si = P[dir_index<L>(cx, cy, cz) * HN + o];
+                const T ti = P[Q * HN + o];
+                const T w = T(L::w(cx, cy, cz));
+                T qd = s0;
+                if (cx) qd += T(4.5) * Ap[0];
+                if (cy) qd += T(4.5) * Ap[1];
+                if (cz) qd += T(4.5) * Ap[2];
+                if (cx * cy) qd += T(9 * cx * cy) * Ap[3];
+                if (cx * cz) qd += T(9 * cx * cz) * Ap[4];
+                if (cy * cz) qd += T(9 * cy * cz) * Ap[5];
+                const T gi = w * (qd + T(3 * cx) * jx + T(3 * cy) * jy + T(3 * cz) * jz);
+                l_r1r += ti * (w + gi);
+                if (cx || cy || cz) {
+                    const T il = T(inv_len_c(cx, cy, cz));
+                    const T cn = T(cx) * nv[0] + T(cy) * nv[1] + T(cz) * nv[2];
+                    l_e += ti * w * cn * il;
+                    const T f = ti * e * w * il;
+                    ln[0] += f * T(cx);
+                    ln[1] += f * T(cy);
+                    ln[2] += f * T(cz);
+                }
+                const T ws = w * (si + ti * r1r);
+                ld += ws;
+                lj[0] += T(3 * cx) * ws;
+                lj[1] += T(3 * cy) * ws;
+                lj[2] += T(3 * cz) * ws;
+                la[0] += (T(4.5 * cx * cx) - T(1.5)) * ws;
+                la[1] += (T(4.5 * cy * cy) - T(1.5)) * ws;
+                la[2] += (T(4.5 * cz * cz) - T(1.5)) * ws;
+                la[3] += T(9 * cx * cy) * ws;
+                la[4] += T(9 * cx * cz) * ws;
+                la[5] += T(9 * cy * cz) * ws;
+            }
+    T l_rinv = T(0), l_ks = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        l_rinv += om * la[k] * jj[k];
+        l_ks += la[k] * nn[k];
+    }
+    T out[11];
+    out[2] = lj[0] + om * rinv * (T(2) * jx * la[0] + jy * la[3] + jz * la[4]);
+    out[3] = lj[1] + om * rinv * (T(2) * jy * la[1] + jx * la[3] + jz * la[5]);
+    out[4] = lj[2] + om * rinv * (T(2) * jz * la[2] + jx * la[4] + jy * la[5]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[5 + k] = (T(1) - om) * la[k];
+    ln[0] += ks * (T(2) * nv[0] * la[0] + nv[1] * la[3] + nv[2] * la[4]);
+    ln[1] += ks * (T(2) * nv[1] * la[1] + nv[0] * la[3] + nv[2] * la[5]);
+    ln[2] += ks * (T(2) * nv[2] * la[2] + nv[0] * la[4] + nv[1] * la[5]);
+    const T l_gn = p.A_s * T(1.0 / 9.0) * l_ks - (ln[0] * G[0] + ln[1] * G[1] + ln[2] * G[2]) / (gn * gn);
+    l_rinv += l_r1r * r1 - l_e * p.beta * r1 * r1;
+    out[0] = l_r1r * rinv + l_e * p.beta * (T(1) - T(2) * r1 * rinv);
+    out[1] = ld - l_rinv * rinv * rinv;
+#pragma unroll
+    for (int f = 0; f < 11; ++f) lam[f * fs + i0] = out[f];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lam_g[a * fs + i0] = ln[a] / gn + l_gn * G[a] / gn;
+    double part = 0.0;
+    for (int k = 0; k < 6; ++k) part += (double)la[k] * ((double)jj[k] * (double)rinv - (double)A[k]);
+    return part;
+}
+
+template <class L, class T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY, (AdjTile<L, T, BX, BY>::MINB))
+    k_adjoint_cg_tiled(const T* __restrict__ lam_new, const T* __restrict__ m, T* __restrict__ lam,
+                       T* __restrict__ lam_g, Layout lay, CGAdjPar<T> p, mom::Sched sc,
+                       double* __restrict__ domega_rows) {
+    using C = AdjTile<L, T, BX, BY>;
+    constexpr int NT = C::NT, HX = C::HX, HN = C::HN, SLOT = C::SLOT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const ring = reinterpret_cast<T*>(smem_raw);
+    const int nx = lay.nx, ny = lay.ny, nz = lay.nz;
+    const size_t fs = lay.fs, plane = (size_t)lay.px * lay.py;
+    const int t = threadIdx.x, tx = t % BX, ty = t / BX;
+    const int n_own = (ty + 1) * HX + (tx + 1);
+    double part = 0.0;
+
+    for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
+        int x0, y0, za, zb;  // receivers of planes za .. zb-1 of the tile at (x0, y0)
+        sc.item(it, BX, BY, nz, x0, y0, za, zb);
+        // region nodes of this thread: j = t and j = t + NT (if inside the tile plus halo)
+        const int j1 = t + NT;
+        const size_t off0 = lay.at(mom::pmod(x0 - 1 + t % HX, nx), mom::pmod(y0 - 1 + t / HX, ny), 0);
+        const size_t off1 = j1 < HN ? lay.at(mom::pmod(x0 - 1 + j1 % HX, nx), mom::pmod(y0 - 1 + j1 / HX, ny), 0) : 0;
+        const int ox = x0 + tx, oy = y0 + ty;
+        const bool ok = ox < nx && oy < ny;
+        const size_t own = ok ? lay.at(ox, oy, 0) : 0;
+        auto slot = [&](int q) { return ring + (size_t)((q - za + 1) % 3) * SLOT; };  // q >= za - 1
+        auto publish = [&](int q) {
+            T* S = slot(q);
+            const size_t zo = (size_t)mom::pmod(q, nz) * plane;
+            adj_publish<L, T, HN>(lam_new, m, lay, off0 + zo, t, S);
+            if (j1 < HN) adj_publish<L, T, HN>(lam_new, m, lay, off1 + zo, j1, S);
+        };
+        publish(za - 1);
+        publish(za);
+        for (int q = za; q < zb; ++q) {  // receivers of plane q
+            publish(q + 1);
+            T sv[11];
+            const size_t iy = own + (size_t)mom::pmod(q, nz) * plane;
+            if (ok && LLB_IN(iy, fs, kChkLoad)) {
+#pragma unroll
+                for (int f = 0; f < 11; ++f) sv[f] = m[f * fs + iy];
+            }
+            __syncthreads();  // planes q - 1, q, q + 1 published
+            if (ok) part += adj_receive<L, T, HX, HN>(slot(q - 1), slot(q), slot(q + 1), n_own, sv, p, lam, lam_g, iy, fs);
+            __syncthreads();  // the slot of plane q - 1 may be refilled
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    __shared__ double wsum[NT / 32];
+    if ((t & 31) == 0) wsum[t >> 5] = part;
+    __syncthreads();
+    if (t == 0) {
+        double sacc = 0.0;
+        for (int w = 0; w < NT / 32; ++w) sacc += wsum[w];
+        domega_rows[blockIdx.x] = sacc;
+    }
+}
+
 // acc += sum of rows (one block, fixed order).
 __global__ void k_sum_rows(const double* __restrict__ rows, size_t n, double* __restrict__ acc) {
     __shared__ double sh[256];
@@ -405,17 +650,43 @@ cudaError_t adj_step(const llb_ctx& c, const void* lam_new, const void* m, void*
                                 : adj_step_t<D3Q27, float>(c, lam_new, m, lam, rows);
 }
 
+// CTAs of the tiled first pass for this context (0 if it cannot run).
+template <class L, class T>
+int adj_tiled_ctas(const llb_ctx& c) {
+    using C = AdjTile<L, T, kAdjBX, kAdjBY>;
+    auto kern = k_adjoint_cg_tiled<L, T, kAdjBX, kAdjBY>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::smem_bytes) != cudaSuccess || per_sm < 1)
+        return 0;
+    const mom::Sched sc = mom::plan(c.nx, c.ny, c.nz, kAdjBX, kAdjBY, per_sm * c.num_sms);
+    return std::min(sc.nitems, per_sm * c.num_sms);
+}
+
+// One two-component adjoint step; *nrows: rows of dL/domega partial sums written.
 template <class L, class T>
 cudaError_t adj_cg_step_t(const llb_ctx& c, const void* lam_new, const void* m, void* lam, void* lam_g,
-                          double* rows) {
+                          double* rows, size_t* nrows) {
     CGAdjPar<T> p;
     p.omega = (T)c.omega;
     p.beta = (T)c.params.beta;
     p.A_s = (T)c.params.A_s;
     p.eps2 = (T)(c.params.grad_eps * c.params.grad_eps);
-    k_adjoint_cg_local<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(
-        static_cast<const T*>(lam_new), static_cast<const T*>(m), static_cast<T*>(lam), static_cast<T*>(lam_g), c.lay,
-        p, rows);
+    const int grid = (c.params.debug_flags & 2) ? 0 : adj_tiled_ctas<L, T>(c);
+    if (grid > 0) {
+        using C = AdjTile<L, T, kAdjBX, kAdjBY>;
+        const mom::Sched sc = mom::plan(c.nx, c.ny, c.nz, kAdjBX, kAdjBY, grid);
+        k_adjoint_cg_tiled<L, T, kAdjBX, kAdjBY><<<grid, C::NT, C::smem_bytes, c.stream>>>(
+            static_cast<const T*>(lam_new), static_cast<const T*>(m), static_cast<T*>(lam), static_cast<T*>(lam_g),
+            c.lay, p, sc, rows);
+        *nrows = (size_t)grid;
+    } else {  // reference form: one thread per node, neighbour fields loaded directly
+        k_adjoint_cg_local<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(
+            static_cast<const T*>(lam_new), static_cast<const T*>(m), static_cast<T*>(lam), static_cast<T*>(lam_g),
+            c.lay, p, rows);
+        *nrows = (size_t)adj_grid(c).x * c.ny * c.nz;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adjoint_cg_phi<L, T><<<adj_grid(c), kAdjThreads, 0, c.stream>>>(static_cast<const T*>(m),
@@ -424,12 +695,13 @@ cudaError_t adj_cg_step_t(const llb_ctx& c, const void* lam_new, const void* m, 
     return cudaGetLastError();
 }
 
-cudaError_t adj_cg_step(const llb_ctx& c, const void* lam_new, const void* m, void* lam, void* lam_g, double* rows) {
+cudaError_t adj_cg_step(const llb_ctx& c, const void* lam_new, const void* m, void* lam, void* lam_g, double* rows,
+                        size_t* nrows) {
     if (c.Q == 19)
-        return c.storage == LLB_F64 ? adj_cg_step_t<D3Q19, double>(c, lam_new, m, lam, lam_g, rows)
-                                    : adj_cg_step_t<D3Q19, float>(c, lam_new, m, lam, lam_g, rows);
-    return c.storage == LLB_F64 ? adj_cg_step_t<D3Q27, double>(c, lam_new, m, lam, lam_g, rows)
-                                : adj_cg_step_t<D3Q27, float>(c, lam_new, m, lam, lam_g, rows);
+        return c.storage == LLB_F64 ? adj_cg_step_t<D3Q19, double>(c, lam_new, m, lam, lam_g, rows, nrows)
+                                    : adj_cg_step_t<D3Q19, float>(c, lam_new, m, lam, lam_g, rows, nrows);
+    return c.storage == LLB_F64 ? adj_cg_step_t<D3Q27, double>(c, lam_new, m, lam, lam_g, rows, nrows)
+                                : adj_cg_step_t<D3Q27, float>(c, lam_new, m, lam, lam_g, rows, nrows);
 }
 
 int grid_n(const llb_ctx& c) {
@@ -451,6 +723,9 @@ cudaError_t fwd_one(llb_ctx* c) {
 }
 
 }  // namespace
+
+LLB_CHK_TU(adjoint)
+
 }  // namespace llb
 
 extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gfinal, void* dev_ginit, int dtype,
@@ -467,7 +742,9 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     const int K = every > 0 ? every : (int)std::fmax(1.0, std::round(std::sqrt((double)nsteps)));
     const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
     const size_t sb = c->state_bytes;
-    const size_t nrows = (size_t)adj_grid(*c).x * c->ny * c->nz;
+    // rows of dL/domega partial sums: one per block of the one-thread-per-node kernels,
+    // or one per CTA of the tiled first pass (at most 32 per SM)
+    const size_t nrows = std::max((size_t)adj_grid(*c).x * c->ny * c->nz, (size_t)32 * (c->num_sms > 0 ? c->num_sms : 1));
     // scratch: nseg checkpoints, K segment states, two cotangents, omega rows, accumulator
     std::vector<void*> ptrs;
     auto grab = [&](size_t bytes) -> void* {
@@ -527,10 +804,11 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
             if (e == cudaSuccess && s + 1 < s1) e = fwd_one(c);
         }
         for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
-            e = two ? adj_cg_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, lamG, rows)
+            size_t used = (size_t)adj_grid(*c).x * c->ny * c->nz;
+            e = two ? adj_cg_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, lamG, rows, &used)
                     : adj_step(*c, lam_in, seg + (size_t)(s - s0) * sb, lam_out, rows);
             if (e == cudaSuccess) {
-                k_sum_rows<<<1, 256, 0, c->stream>>>(rows, nrows, acc);
+                k_sum_rows<<<1, 256, 0, c->stream>>>(rows, used, acc);
                 e = cudaGetLastError();
             }
             void* tmp = lam_in;

@@ -79,7 +79,7 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     if (p.variant < 0 || p.variant >= kTiledVariants32) { *why = "variant out of range"; return LLB_EINVAL; }
     if (p.ncomp == 2 && p.variant >= kCGVariants) { *why = "two-component variant out of range"; return LLB_EINVAL; }
     if (p.wait_budget_ms < 1 || p.wait_budget_ms > 600000) { *why = "wait_budget_ms must be in 1..600000"; return LLB_EINVAL; }
-    if (p.debug_flags & ~1) { *why = "unknown debug flag"; return LLB_EINVAL; }
+    if (p.debug_flags & ~3) { *why = "unknown debug flag"; return LLB_EINVAL; }
     if (!(p.grad_eps >= 0.0) || !std::isfinite(p.grad_eps)) { *why = "grad_eps must be finite and >= 0"; return LLB_EINVAL; }
     if (p.ncomp == 2) {
         if (nx < 4 || ny < 4 || nz < 4) { *why = "two components need nx, ny, nz >= 4"; return LLB_EINVAL; }
@@ -601,7 +601,7 @@ int llb_checked_status(int* enabled, int* site, long long* index) {
                                              llb::chk_take_tiled_f16, llb::chk_take_tiled_bf16,
                                              llb::chk_take_step,      llb::chk_take_tma,
                                              llb::chk_take_cg,        llb::chk_take_cg_batch,
-                                             llb::chk_take_pop};
+                                             llb::chk_take_pop,       llb::chk_take_adjoint};
     int first = 0;
     long long first_i = 0;
     bool failed = false;

@@ -131,6 +131,7 @@ int chk_take_tma(int* site, long long* index);
 int chk_take_cg(int* site, long long* index);
 int chk_take_cg_batch(int* site, long long* index);
 int chk_take_pop(int* site, long long* index);
+int chk_take_adjoint(int* site, long long* index);
 
 // Population-storing baselines (population_step.cu)
 cudaError_t launch_population_step(const llb_ctx& c, const void* in, void* out, bool bgk);

@@ -205,7 +205,34 @@ def batches():
                 _case(name, fn, TOL[storage] if storage == llb.LLB_F64 else 1e-4)
 
 
-GROUPS = {"one": one_component, "two": two_component, "pop": populations, "batch": batches}
+def adjoints():
+    """Two-component adjoint (tiled first pass) against its reference form."""
+    import torch
+    for q in (19, 27):
+        for shape in [(4, 4, 4), (9, 6, 5), (37, 11, 7)]:
+            sh = "x".join(map(str, shape))
+            m0 = _drops(shape)
+            g = np.random.default_rng(3).uniform(-1, 1, m0.shape)
+            for storage in (llb.LLB_F64, llb.LLB_F32):
+                def fn(storage=storage):
+                    res = []
+                    for flags in (0, 2):
+                        p = llb.llb_params_default(storage=storage, ncomp=2, beta=CG.beta, A_s=CG.A_s, A_h=0.0,
+                                                   grad_eps=0.02, debug_flags=flags)
+                        ctx = llb.llb_create(*shape, q, TAU_2, p)
+                        try:
+                            llb.llb_init_moments(ctx, m0)
+                            gfin = torch.from_numpy(g).cuda()
+                            gini = torch.empty_like(gfin)
+                            llb.llb_adjoint(ctx, STEPS, gfin, gini, every=2)
+                            res.append(gini.cpu().numpy())
+                        finally:
+                            llb.llb_destroy(ctx)
+                    return res[0], res[1]
+                _case(f"d3q{q}-{sh}-adjoint-{SNAME[storage]}", fn, TOL[storage])
+
+
+GROUPS = {"one": one_component, "two": two_component, "pop": populations, "batch": batches, "adjoint": adjoints}
 
 if __name__ == "__main__":
     for g in (sys.argv[1:] or list(GROUPS)):

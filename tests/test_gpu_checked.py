@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # least number of cases each group must actually run (not skipped as unsupported)
-MIN_RUN = {"one": 140, "two": 50, "pop": 30, "batch": 10}
+MIN_RUN = {"one": 140, "two": 50, "pop": 30, "batch": 10, "adjoint": 12}
 
 
 def _run_group(group):
