@@ -3,7 +3,9 @@
 // different sizes).  Each box is an ordinary context (its own state copies,
 // initialisation, read-back and diagnostics); the batch adds one device table
 // of boxes per flip-flop parity and the launch that walks every box's work
-// items in one grid.
+// items in one grid.  The CTAs take items from a work queue (a counter zeroed
+// before each launch), so that the items of boxes of different sizes, which
+// differ in length, even out over the grid.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -17,6 +19,7 @@ struct llb_batch {
     int n = 0;
     std::vector<llb_ctx*> ctx;
     llb::BatchDom* dev_doms[2] = {nullptr, nullptr};
+    int* dev_next = nullptr;  // work queue: next item to take (zeroed before every launch)
     int total = 0;   // work items over all boxes
     int grid = 0;    // persistent CTAs
     int variant = 0;
@@ -63,6 +66,11 @@ int build_tables(llb_batch* b) {
             h[k][d].out = c->buf[1 - k];
         }
     }
+    if (!b->dev_next && cudaMalloc(&b->dev_next, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        b->dev_next = nullptr;
+        return LLB_ENOMEM;
+    }
     for (int k = 0; k < 2; ++k) {
         if (!b->dev_doms[k] && cudaMalloc(&b->dev_doms[k], sizeof(llb::BatchDom) * b->n) != cudaSuccess) {
             cudaGetLastError();
@@ -82,7 +90,9 @@ int build_tables(llb_batch* b) {
 }
 
 cudaError_t launch(llb_batch* b, int parity) {
-    return llb::launch_cg_batch(*b->ctx[0], b->dev_doms[parity], b->n, b->total, b->grid);
+    const cudaError_t e = cudaMemsetAsync(b->dev_next, 0, sizeof(int), b->ctx[0]->stream);
+    if (e != cudaSuccess) return e;
+    return llb::launch_cg_batch(*b->ctx[0], b->dev_doms[parity], b->n, b->total, b->grid, b->dev_next);
 }
 
 void advance(llb_batch* b, int nsteps) {
@@ -141,6 +151,7 @@ void llb_batch_destroy(llb_batch* b) {
     drop_graphs(b);
     for (int k = 0; k < 2; ++k)
         if (b->dev_doms[k]) cudaFree(b->dev_doms[k]);
+    if (b->dev_next) cudaFree(b->dev_next);
     for (llb_ctx* c : b->ctx) {
         c->in_batch = false;
         llb_destroy(c);

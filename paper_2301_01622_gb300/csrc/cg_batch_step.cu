@@ -30,10 +30,10 @@ void cg_batch_plan_v(const llb_ctx& c, int grid, BatchDom* d) {
 }
 
 template <class L, class T, class V>
-cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid) {
+cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid, int* next) {
     using C = CGCfg<L, T, V::BX, V::BY>;
     k_cg_batch<L, T, V::BX, V::BY, V::MINB, V::FAST, V::ROLLED><<<grid, C::NT, C::smem_bytes, c.stream>>>(
-        doms, ndom, total, cg_params<T>(c));
+        doms, ndom, total, cg_params<T>(c), next);
     return cudaGetLastError();
 }
 
@@ -41,8 +41,8 @@ cudaError_t cg_batch_run_v(const llb_ctx& c, const BatchDom* doms, int ndom, int
 
 int cg_batch_ctas(const llb_ctx& c) { LLB_CG(cg_batch_ctas_v, c) }
 void cg_batch_plan(const llb_ctx& c, int grid, BatchDom* d) { LLB_CG(cg_batch_plan_v, c, grid, d) }
-cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid) {
-    LLB_CG(cg_batch_run_v, c, doms, ndom, total, grid)
+cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid, int* next) {
+    LLB_CG(cg_batch_run_v, c, doms, ndom, total, grid, next)
 }
 
 LLB_CHK_TU(cg_batch)

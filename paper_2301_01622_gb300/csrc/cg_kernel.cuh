@@ -613,8 +613,16 @@ __global__ void __launch_bounds__(BX * BY, MINB)
 // launch; a CTA finds the box of each item by binary search on item_begin.
 template <class L, class T, int BX, int BY, int MINB, bool FAST, bool ROLLED>
 __global__ void __launch_bounds__(BX * BY, MINB)
-    k_cg_batch(const BatchDom* __restrict__ doms, int ndom, int total, CGPar<T> prm) {
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    k_cg_batch(const BatchDom* __restrict__ doms, int ndom, int total, CGPar<T> prm, int* __restrict__ next) {
+    // work queue: each CTA takes the next item when it is done with one, so that
+    // items of different lengths (boxes of different sizes) even out over the grid
+    __shared__ int s_it;
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = s_it;
+        __syncthreads();  // every thread has read s_it before it is overwritten
+        if (it >= total) break;
         int lo = 0, hi = ndom - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

@@ -118,7 +118,8 @@ struct BatchDom {
 int cg_batch_ctas(const llb_ctx& c);
 // Fill the schedule fields of d for box c (c.nx.. give the box size) and `grid` CTAs.
 void cg_batch_plan(const llb_ctx& c, int grid, BatchDom* d);
-cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid);
+// `next`: work-queue counter, zero at launch.
+cudaError_t launch_cg_batch(const llb_ctx& c, const BatchDom* doms, int ndom, int total, int grid, int* next);
 
 // Bounds-check records of the kernel translation units (checked build; the
 // normal build reports none).  Read and clear; -1 if the copy fails.
