@@ -798,10 +798,18 @@ extern "C" int llb_adjoint(llb_ctx* c, int nsteps, int every, const void* dev_gf
     for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
         const int s0 = k * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
         // recompute the states s0 .. s1-1 of this segment from its checkpoint
-        e = cudaMemcpyAsync(c->buf[c->cur], ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, c->stream);
-        for (int s = s0; s < s1 && e == cudaSuccess; ++s) {
-            e = cudaMemcpyAsync(seg + (size_t)(s - s0) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream);
-            if (e == cudaSuccess && s + 1 < s1) e = fwd_one(c);
+        if (two) {
+            // the two-component step takes any pair of state buffers: step slot to slot
+            e = cudaMemcpyAsync(seg, ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, c->stream);
+            for (int s = s0; s + 1 < s1 && e == cudaSuccess; ++s)
+                e = launch_cg_tiled(*c, seg + (size_t)(s - s0) * sb, seg + (size_t)(s + 1 - s0) * sb);
+        } else {
+            e = cudaMemcpyAsync(c->buf[c->cur], ck + (size_t)k * sb, sb, cudaMemcpyDeviceToDevice, c->stream);
+            for (int s = s0; s < s1 && e == cudaSuccess; ++s) {
+                e = cudaMemcpyAsync(seg + (size_t)(s - s0) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice,
+                                    c->stream);
+                if (e == cudaSuccess && s + 1 < s1) e = fwd_one(c);
+            }
         }
         for (int s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
             size_t used = (size_t)adj_grid(*c).x * c->ny * c->nz;
