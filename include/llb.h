@@ -288,7 +288,12 @@ LLB_API int llb_synchronize(llb_ctx* ctx);
 LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
 
 /* Device pointer of the current state copy, its element type and the kernel
- * the context runs (for profiling and zero-copy views). */
+ * the context runs (for profiling and zero-copy views).  Bit-for-bit
+ * checkpoint: the current state copy (llb_state_bytes bytes: the shifted
+ * moments in the context's padded layout, ghost copies included), saved and
+ * later written into the current state copy of a context created with the
+ * same sizes and parameters (after its llb_init_*), resumes the run bit for
+ * bit; llb_steps_done then counts from that restart. */
 LLB_API int llb_state_device(const llb_ctx* ctx, void** dev_ptr, int* dtype, int* kernel);
 
 /* Adjoint of nsteps moment-only steps (FP32 or FP64 state): the gradient of

@@ -281,6 +281,51 @@ def test_checkpoint_restart(q):
     assert_groups(rest, full, 1e-14, what="restart")
 
 
+@pytest.mark.parametrize("ncomp", [1, 2])
+@pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64], ids=["f32", "f64"])
+def test_bit_identical_restart_from_the_raw_state(storage, ncomp):
+    """A checkpoint of the raw state copy (caller-owned buffers, saved after
+    15 steps and written into a fresh context's current copy) resumes the run
+    bit for bit: 15 + 15 steps equal 30 continuous steps exactly."""
+    torch = pytest.importorskip("torch")
+    n, q, tau = 24, 27 if ncomp == 2 else 19, 0.8
+    if ncomp == 2:
+        r1, r2, u = inputs.droplets(n, n, n, [(8.0, 11.5, 12.0), (16.0, 12.5, 12.0)], [3.5, 3.5],
+                                    [(0.03, 0, 0), (-0.03, 0, 0)])
+        tot = lb.equilibrium_moments(r1 + r2, u)
+        m0 = np.ascontiguousarray(np.concatenate([r1[None], r2[None], tot[1:]]))
+        kw = dict(ncomp=2, beta=0.7, A_s=0.02, A_h=0.01)
+    else:
+        m0 = lb.equilibrium_moments(*inputs.taylor_green_3d(n, n, n, u0=0.05, noise=1e-3, seed=3))
+        kw = {}
+    dt = torch.float32 if storage == llb.LLB_F32 else torch.float64
+    nbytes = llb.llb_state_bytes(n, n, n, q, llb.llb_params_default(storage=storage, **kw))
+
+    def run(steps, restore=None):
+        bufs = [torch.zeros(nbytes // (4 if storage == llb.LLB_F32 else 8), dtype=dt, device="cuda")
+                for _ in range(2)]
+        ctx = llb.llb_create(n, n, n, q, tau, llb.llb_params_default(storage=storage, buffers=bufs, **kw))
+        try:
+            llb.llb_init_moments(ctx, m0)
+            cur = next(b for b in bufs if b.data_ptr() == llb.llb_state_device(ctx)[0])
+            if restore is not None:
+                torch.cuda.synchronize()
+                cur.copy_(restore)
+                torch.cuda.synchronize()
+            llb.llb_step(ctx, steps)
+            llb.llb_synchronize(ctx)
+            saved = next(b for b in bufs if b.data_ptr() == llb.llb_state_device(ctx)[0]).clone()
+            out = llb.llb_get_moments(ctx, np.empty(m0.shape))
+        finally:
+            llb.llb_destroy(ctx)
+        return saved, out
+
+    _, full = run(30)
+    half, _ = run(15)
+    _, rest = run(15, restore=half)
+    assert np.array_equal(rest, full)
+
+
 def test_device_buffers_and_stream_from_torch():
     """Caller-owned device buffers and a caller stream (torch), device-side init/get."""
     torch = pytest.importorskip("torch")
