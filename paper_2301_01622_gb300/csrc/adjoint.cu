@@ -23,6 +23,11 @@
 // lam_phi(z) = 3 sum_k w_k c_k . lam_G(z - c_k), added through phi(z) to
 // lam_rho1(z) and lam_d(z).
 //
+// For two components the first pass (everything but the transposed gradient
+// stencil) runs tiled by default (k_adjoint_cg_tiled, below); one component
+// keeps the one-thread-per-node k_adjoint_step, a plain linear gather whose
+// neighbour loads hit L1 (a tiled form of it measured 13-18 % slower).
+//
 // llb_adjoint runs the forward steps once, keeping the state every K steps
 // (moments only), then walks the segments backwards: each segment is
 // recomputed from its checkpoint with its K states kept, and the adjoint
