@@ -85,6 +85,24 @@ def random_moments(nx: int, ny: int, nz: int, seed: int = 1, nfields: int = 10,
     raise ValueError("nfields must be 10 or 11")
 
 
+def random_moments_device(nx: int, ny: int, nz: int, seed: int = 1, rho_spread: float = 0.05,
+                          j_amp: float = 0.03, p_diag=(0.30, 0.37), p_off: float = 0.01):
+    """The random_moments recipe (one component) drawn on the GPU with a seeded
+    torch generator, as a float32 device tensor of shape (10, nz, ny, nx): for
+    boxes whose inputs are too large to build on the host."""
+    import torch
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    m = torch.empty((10, nz, ny, nx), dtype=torch.float32, device="cuda")
+    ranges = [(1.0 - rho_spread, 1.0 + rho_spread)] + [(-j_amp, j_amp)] * 3 + [tuple(p_diag)] * 3 + \
+             [(-p_off, p_off)] * 3
+    for f, (lo, hi) in enumerate(ranges):
+        torch.rand(m[f].shape, generator=g, device="cuda", out=m[f])
+        m[f].mul_(hi - lo).add_(lo)
+    return m
+
+
 def point_perturbation(nx: int, ny: int, nz: int, at=(0, 0, 0), delta: float = 0.1, rho0: float = 1.0):
     """Fluid at rest with rho = rho0 everywhere except rho0 + delta at node ``at`` = (x, y, z)."""
     rho = np.full((nz, ny, nx), rho0, dtype=np.float64)
