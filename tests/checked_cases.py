@@ -4,7 +4,8 @@ LLB_CHECKED=1 (libllb_checked.so loaded instead of libllb.so).
 Every case runs a few steps of one kernel on a small, mostly ragged box (tiles
 that stick out of the box in x and y, boxes smaller than one tile, a z extent
 shorter than a work chunk), then asks the library for the first out-of-range
-index its kernels recorded, and compares the moments with the FP64 oracle.
+index its kernels recorded, and compares the moments with the FP64 oracle (the
+adjoint cases: the tiled first pass with its reference form).
 Prints one JSON object per case:
   {"case": name, "site": s, "index": i, "err": e, "tol": t, "skip": why|null}
 Called by tests/test_gpu_checked.py; not a test module itself.
