@@ -314,9 +314,13 @@ def droplet_arm(args, llb, inputs, stream, world, peak, A_h, label):
         p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F32, A_h=A_h, A_s=0.01, beta=0.7, stream=stream,
                                    scheme=scheme, variant=getattr(args, "cg_variant", 0) if key == "moment" else 0)
         ctx = llb.llb_create(nx, ny, nz, 27, 1.0, p)
+        e2e = None
         try:
             llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)
             ms, _ = time_steps(llb, ctx, steps, max(3, args.warmup), world)
+            if key == "moment":
+                llb.llb_init_equilibrium(ctx, np.stack([r1, r2]), u)  # end to end from the initial field
+                e2e = droplet_e2e(args, llb, ctx, (11, nz, ny, nx), world)
         finally:
             llb.llb_destroy(ctx)
         ms = reduce_max(ms, world)
@@ -324,11 +328,42 @@ def droplet_arm(args, llb, inputs, stream, world, peak, A_h, label):
         gbs = bpn * nodes / t / 1e9
         out[key] = {"mlups": world * nodes / t / 1e6, "frac": gbs / peak, "achieved_gbs": gbs, "bytes_per_node": bpn,
                     "ms_per_step": ms / steps, "steps": steps}
+        if e2e is not None:
+            out[key]["e2e"] = e2e
     line = dict(out["moment"])
     line["workload"] = f"384x192x192 D3Q27 two-component CG, FP32, tau=1, R=30, U=+-0.05, b=0.5R, A_h={A_h} ({label})"
     line["population_bgk"] = out["population_bgk"]
     line["speedup_vs_population"] = out["moment"]["mlups"] / out["population_bgk"]["mlups"]
     return line
+
+
+def droplet_e2e(args, llb, ctx, shape, world):
+    """One step end to end through llb_step_host: pinned host canonical FP32
+    moments (11 fields) in, one step, moments out, the slab copies overlapped
+    with the per-slab steps; `args.e2e_steps` timed calls."""
+    import torch
+    dev = torch.empty(shape, dtype=torch.float32, device="cuda")
+    llb.llb_get_moments_device(ctx, dev)
+    h_in = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    h_out = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    h_in.copy_(dev)
+    del dev
+    torch.cuda.synchronize()
+    k = max(1, args.e2e_steps)
+    for _ in range(2):
+        llb.llb_step_host(ctx, h_in, h_out, 1)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        llb.llb_step_host(ctx, h_in, h_out, 1)
+    torch.cuda.synchronize()
+    dt = reduce_max(time.perf_counter() - t0, world)
+    nodes = shape[1] * shape[2] * shape[3]
+    nbytes = 11 * nodes * 4
+    return {"value": world * nodes * k / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": k,
+            "path": "llb_step_host(host in, 1 step, host out), FP32 canonical (11 fields), pinned, copies overlapped "
+                    "with per-slab steps"}
 
 
 def ensemble_arm(args, llb, inputs, stream, world, peak):

@@ -194,7 +194,9 @@ LLB_API void llb_destroy(llb_ctx* ctx);
 /* Load canonical moments (layout above) from HOST memory of element type
  * host_dtype (LLB_F64 or LLB_F32).  Copies through a device staging buffer
  * and converts on the device.  Rejects rho <= 0 or non-finite input with
- * LLB_EUNSTABLE (checked on the device, the call synchronises).  Resets the
+ * LLB_EUNSTABLE (checked on the device, the call synchronises; for two
+ * components rho is the total density, and a colour density may be slightly
+ * negative, as a stepped field's can be near interfaces).  Resets the
  * step counter to 0. */
 LLB_API int llb_init_moments(llb_ctx* ctx, const void* host_m, int host_dtype);
 
@@ -273,7 +275,9 @@ LLB_API int llb_diagnostics_noalloc(const void* dev_m, int dtype, int nx, int ny
  * copies out run on three streams of the context, ordered by events, so the
  * call takes about as long as the larger of the two host copies.  With
  * nsteps > 1 only the first step overlaps the copies in and the last step
- * the copies out.  One-component moment-only contexts on the tiled kernel;
+ * the copies out.  Moment-only contexts on the tiled kernels, one component
+ * and two (for two components every slab is at least as thick as the planes
+ * the phase-field gradient and the near-contact probes reach, 2 and 1 + h_c);
  * other contexts get the same result without the overlap.  Page-locked host
  * buffers let the copies run asynchronously.  host_in and host_out stay
  * owned by the caller and must not overlap.  Starts after the work already

@@ -435,11 +435,12 @@ struct CGCfg {
     static_assert(NJ <= 3, "phi region must fit three nodes per thread");
 };
 
-// One work item (z-chunk of one tile) of the two-component step.  Called by
+// One work item (z-chunk of one tile) of the two-component step; the items
+// cover output planes zlo .. zlo + nzr - 1 (the whole box: 0, nz).  Called by
 // every thread of the CTA (it synchronises the CTA).
 template <class L, class T, int BX, int BY, bool FAST, bool ROLLED>
 __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict__ out, const Layout& lay,
-                                        const CGPar<T>& prm, const Sched2& sc, int it) {
+                                        const CGPar<T>& prm, const Sched2& sc, int it, int zlo, int nzr) {
     using C = CGCfg<L, T, BX, BY>;
     constexpr int NT = C::NT, HX1 = C::HX1, HN1 = C::HN1, HX2 = C::HX2, HN2 = C::HN2, NS = C::NS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -461,7 +462,7 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
 
     const int chunk = it / sc.ntiles, tile = it - chunk * sc.ntiles;
     const int x0 = (tile % sc.ncx) * BX, y0 = (tile / sc.ncx) * BY;
-    const int za = chunk * sc.zc, zb = min(nz, za + sc.zc);
+    const int za = zlo + chunk * sc.zc, zb = min(zlo + nzr, za + sc.zc);
     const bool store_ok = (x0 + tx < nx) && (y0 + ty < ny);
     const int gx1 = pmod2(x0 + tx, nx), gy1 = pmod2(y0 + ty, ny);
     const int gx2 = pmod2(x0 - 1 + hx2, nx), gy2 = pmod2(y0 - 1 + hy2, ny);
@@ -604,9 +605,9 @@ __device__ __forceinline__ void cg_item(const T* __restrict__ in, T* __restrict_
 
 template <class L, class T, int BX, int BY, int MINB, bool FAST, bool ROLLED>
 __global__ void __launch_bounds__(BX * BY, MINB)
-    k_cg_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, CGPar<T> prm, Sched2 sc) {
+    k_cg_tiled(const T* __restrict__ in, T* __restrict__ out, Layout lay, CGPar<T> prm, Sched2 sc, int zlo, int nzr) {
     for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x)
-        cg_item<L, T, BX, BY, FAST, ROLLED>(in, out, lay, prm, sc, it);
+        cg_item<L, T, BX, BY, FAST, ROLLED>(in, out, lay, prm, sc, it, zlo, nzr);
 }
 
 // Batched ensemble: the items of every box, box after box, in one persistent
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         sc.zc = d.zc;
         sc.nitems = d.nitems;
         cg_item<L, T, BX, BY, FAST, ROLLED>(static_cast<const T*>(d.in), static_cast<T*>(d.out), d.lay, prm, sc,
-                                    it - d.item_begin);
+                                    it - d.item_begin, 0, d.lay.nz);
     }
 }
 

@@ -121,14 +121,16 @@ __device__ __forceinline__ void put11(T* __restrict__ st, const Layout& L, int x
 
 template <class T>
 __global__ void k_canon_to_shifted2(const void* __restrict__ canon, int cdt, T* __restrict__ st, Layout L,
-                                    int* bad) {
+                                    int* bad, size_t i0, size_t i1) {
     const size_t N = (size_t)L.nx * L.ny * L.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < i1; i += (size_t)gridDim.x * blockDim.x) {
         double v[11];
 #pragma unroll
         for (int f = 0; f < 11; ++f) v[f] = rdt(canon, f * N + i, cdt);
         const double rho = v[0] + v[1];
-        bool b = bad_rho(rho) || !(v[0] >= 0.0) || !(v[1] >= 0.0);
+        // the total density must be positive; a colour density may dip slightly
+        // below zero (the stepped colour-gradient field does so near interfaces)
+        bool b = bad_rho(rho) || !isfinite(v[0]) || !isfinite(v[1]);
 #pragma unroll
         for (int f = 2; f < 11; ++f) b = b || !isfinite(v[f]);
         if (b && bad) atomicOr(bad, 1);
@@ -141,9 +143,10 @@ __global__ void k_canon_to_shifted2(const void* __restrict__ canon, int cdt, T* 
 }
 
 template <class T>
-__global__ void k_shifted_to_canon2(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L) {
+__global__ void k_shifted_to_canon2(const T* __restrict__ st, void* __restrict__ canon, int cdt, Layout L, size_t i0,
+                                    size_t i1) {
     const size_t N = (size_t)L.nx * L.ny * L.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < i1; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         decode(L, i, x, y, z);
         const size_t j = L.at(x, y, z);
@@ -165,7 +168,7 @@ __global__ void k_equilibrium2(const void* __restrict__ rho_p, const void* __res
         const double r1 = rdt(rho_p, i, dt), r2 = rdt(rho_p, N + i, dt);
         const double rho = r1 + r2;
         const double ux = rdt(u_p, i, dt), uy = rdt(u_p, N + i, dt), uz = rdt(u_p, 2 * N + i, dt);
-        if ((bad_rho(rho) || !(r1 >= 0.0) || !(r2 >= 0.0) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) && bad)
+        if ((bad_rho(rho) || !isfinite(r1) || !isfinite(r2) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) && bad)
             atomicOr(bad, 1);
         const double o[11] = {r1, rho - 1.0, rho * ux, rho * uy, rho * uz, rho * ux * ux, rho * uy * uy,
                               rho * uz * uz, rho * ux * uy, rho * ux * uz, rho * uy * uz};
@@ -195,9 +198,11 @@ cudaError_t launch_canonical_to_shifted(const llb_ctx& c, const void* canon, int
     }
     if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
-            k_canon_to_shifted2<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad);
+            k_canon_to_shifted2<double><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<double*>(st), c.lay, bad,
+                                                                            0, c.N);
         else
-            k_canon_to_shifted2<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad);
+            k_canon_to_shifted2<float><<<grid_for(c), 256, 0, c.stream>>>(canon, cdt, static_cast<float*>(st), c.lay, bad,
+                                                                           0, c.N);
         return cudaGetLastError();
     }
     if (c.storage == LLB_F64)
@@ -221,9 +226,11 @@ cudaError_t launch_shifted_to_canonical(const llb_ctx& c, const void* st, void* 
     }
     if (c.ncomp == 2) {
         if (c.storage == LLB_F64)
-            k_shifted_to_canon2<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay);
+            k_shifted_to_canon2<double><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const double*>(st), canon, cdt, c.lay,
+                                                                            0, c.N);
         else
-            k_shifted_to_canon2<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay);
+            k_shifted_to_canon2<float><<<grid_for(c), 256, 0, c.stream>>>(static_cast<const float*>(st), canon, cdt, c.lay,
+                                                                           0, c.N);
         return cudaGetLastError();
     }
     if (c.storage == LLB_F64)
@@ -239,6 +246,13 @@ cudaError_t launch_canonical_to_shifted_range(const llb_ctx& c, const void* cano
                                               int zhi, cudaStream_t s) {
     const size_t per = (size_t)c.nx * c.ny, i0 = per * zlo, i1 = per * zhi;
     const int grid = (int)std::min<size_t>((i1 - i0 + 255) / 256, (size_t)c.num_sms * 8);
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_canon_to_shifted2<double><<<grid, 256, 0, s>>>(canon, cdt, static_cast<double*>(st), c.lay, bad, i0, i1);
+        else
+            k_canon_to_shifted2<float><<<grid, 256, 0, s>>>(canon, cdt, static_cast<float*>(st), c.lay, bad, i0, i1);
+        return cudaGetLastError();
+    }
     switch (c.storage) {
         case LLB_F64:
             k_canon_to_shifted<double><<<grid, 256, 0, s>>>(canon, cdt, static_cast<double*>(st), c.lay, bad, i0, i1);
@@ -260,6 +274,13 @@ cudaError_t launch_shifted_to_canonical_range(const llb_ctx& c, const void* st, 
                                               cudaStream_t s) {
     const size_t per = (size_t)c.nx * c.ny, i0 = per * zlo, i1 = per * zhi;
     const int grid = (int)std::min<size_t>((i1 - i0 + 255) / 256, (size_t)c.num_sms * 8);
+    if (c.ncomp == 2) {
+        if (c.storage == LLB_F64)
+            k_shifted_to_canon2<double><<<grid, 256, 0, s>>>(static_cast<const double*>(st), canon, cdt, c.lay, i0, i1);
+        else
+            k_shifted_to_canon2<float><<<grid, 256, 0, s>>>(static_cast<const float*>(st), canon, cdt, c.lay, i0, i1);
+        return cudaGetLastError();
+    }
     switch (c.storage) {
         case LLB_F64:
             k_shifted_to_canon<double><<<grid, 256, 0, s>>>(static_cast<const double*>(st), canon, cdt, c.lay, i0, i1);

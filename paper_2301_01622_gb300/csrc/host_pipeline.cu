@@ -17,7 +17,11 @@
 //
 // With nsteps > 1 the first step is pipelined with the copies in, the middle
 // steps are ordinary launches and the last step is pipelined with the copies
-// out.  One-component moment-only contexts on the tiled kernel.
+// out.  Moment-only contexts on the tiled kernels: one component (the pull
+// reaches one plane) and two components (the phase-field gradient of a source
+// node reaches two planes, the near-contact probes 1 + h_c); every slab is at
+// least that thick, so a slab's inputs are still its own and its two
+// neighbours'.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,12 +57,12 @@ int pipe_setup(llb_ctx* c, size_t out_bytes) {
     return LLB_OK;
 }
 
-// Copy the ten fields of planes [z0, z1) between host and device canonical
+// Copy the nf fields of planes [z0, z1) between host and device canonical
 // arrays (field-major, field size N elements of es bytes): one 2D copy when
 // the field stride is within the copy engine's pitch limit, else one copy per
 // field.
-cudaError_t copy_slab(void* dst, const void* src, size_t N, size_t es, size_t off, size_t len, cudaMemcpyKind kind,
-                      cudaStream_t st) {
+cudaError_t copy_slab(void* dst, const void* src, size_t N, size_t es, int nf, size_t off, size_t len,
+                      cudaMemcpyKind kind, cudaStream_t st) {
     static int max_pitch = -1;
     if (max_pitch < 0) {
         int dev = 0, v = 0;
@@ -68,8 +72,8 @@ cudaError_t copy_slab(void* dst, const void* src, size_t N, size_t es, size_t of
     }
     char* d = static_cast<char*>(dst) + off;
     const char* s = static_cast<const char*>(src) + off;
-    if (N * es <= (size_t)max_pitch) return cudaMemcpy2DAsync(d, N * es, s, N * es, len, 10, kind, st);
-    for (int f = 0; f < 10; ++f)
+    if (N * es <= (size_t)max_pitch) return cudaMemcpy2DAsync(d, N * es, s, N * es, len, nf, kind, st);
+    for (int f = 0; f < nf; ++f)
         if (cudaError_t e = cudaMemcpyAsync(d + f * N * es, s + f * N * es, len, kind, st); e != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -99,7 +103,8 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
         c->msg = "llb_step_host: bad argument";
         return LLB_EINVAL;
     }
-    if (c->scheme != LLB_SCHEME_MOMENT || c->ncomp != 1 || c->kernel != LLB_KERNEL_TILED) {
+    const bool two = c->ncomp == 2;
+    if (c->scheme != LLB_SCHEME_MOMENT || (!two && c->kernel != LLB_KERNEL_TILED)) {
         // other schemes and kernels: the same result without the overlap
         int rc = llb_init_moments(c, host_in, host_dtype);
         if (rc == LLB_OK) rc = llb_step(c, nsteps);
@@ -107,7 +112,8 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
         return rc;
     }
     const size_t es = elem_size(host_dtype), N = c->N, plane = (size_t)c->nx * c->ny;
-    const size_t bytes = 10 * N * es;
+    const int nf = two ? 11 : 10;
+    const size_t bytes = (size_t)nf * N * es;
     if (c->staging_bytes < bytes) {
         if (c->staging) {
             cudaStreamSynchronize(c->stream);
@@ -126,7 +132,11 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
         c->msg = "llb_step_host: stream or staging set-up failed";
         return rc;
     }
-    const int K = std::max(1, std::min(kMaxSlabs, c->nz / 8));
+    // planes a slab's step reaches beyond the slab: the pull (1); for two
+    // components the gradient of phi at the source planes (2) and the
+    // near-contact probes (1 + h_c)
+    const int reach = two ? std::max(2, c->params.A_h != 0.0 ? 1 + c->params.h_c : 0) : 1;
+    const int K = std::max(1, std::min(kMaxSlabs, c->nz / std::max(8, reach)));
     int zb[kMaxSlabs + 1];
     for (int k = 0; k <= K; ++k) zb[k] = (int)((long long)k * c->nz / K);
     Events E;
@@ -148,7 +158,7 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
     // copies in: nothing but copies on this stream
     int cur = c->cur;
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
-        e = copy_slab(dev_i, host_in, N, es, slab_off(k), slab_len(k), cudaMemcpyHostToDevice, sin);
+        e = copy_slab(dev_i, host_in, N, es, nf, slab_off(k), slab_len(k), cudaMemcpyHostToDevice, sin);
         if (e == cudaSuccess) e = cudaEventRecord(ev_copied[k], sin);
     }
     int converted = 0;  // input slabs 0 .. converted-1 are in the shifted state
@@ -168,13 +178,14 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
                 }
             }
             if (e == cudaSuccess)
-                e = launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], zb[k], zb[k + 1], scmp);
+                e = two ? launch_cg_tiled_range(*c, c->buf[cur], c->buf[1 - cur], zb[k], zb[k + 1], scmp)
+                        : launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], zb[k], zb[k + 1], scmp);
             if (copy_out && e == cudaSuccess) {
                 e = launch_shifted_to_canonical_range(*c, c->buf[1 - cur], dev_o, host_dtype, zb[k], zb[k + 1], scmp);
                 if (e == cudaSuccess) e = cudaEventRecord(ev_ready[k], scmp);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_ready[k], 0);
                 if (e == cudaSuccess)
-                    e = copy_slab(host_out, dev_o, N, es, slab_off(k), slab_len(k), cudaMemcpyDeviceToHost, sout);
+                    e = copy_slab(host_out, dev_o, N, es, nf, slab_off(k), slab_len(k), cudaMemcpyDeviceToHost, sout);
             }
         }
         cur = 1 - cur;
@@ -183,7 +194,8 @@ extern "C" int llb_step_host(llb_ctx* c, const void* host_in, void* host_out, in
     if (nsteps > 1 && e == cudaSuccess) {
         // middle steps on the step stream, then the last one with the copies out
         for (int s = 1; s < nsteps - 1 && e == cudaSuccess; ++s) {
-            e = launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], 0, c->nz, scmp);
+            e = two ? launch_cg_tiled_range(*c, c->buf[cur], c->buf[1 - cur], 0, c->nz, scmp)
+                    : launch_moment_tiled_range(*c, cur, c->buf[cur], c->buf[1 - cur], 0, c->nz, scmp);
             cur = 1 - cur;
         }
         if (e == cudaSuccess) pipelined_step(false, true);

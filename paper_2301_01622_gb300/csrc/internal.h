@@ -105,6 +105,8 @@ void moment_tiled_box_bf16(const llb_ctx& c, int* w, int* h);
 constexpr int kCGVariants = 6;  // tile / division variants of the two-component kernel
 int cg_tiled_ctas(const llb_ctx& c);
 cudaError_t launch_cg_tiled(const llb_ctx& c, const void* in, void* out);
+// Output planes zlo .. zhi-1 on stream st.
+cudaError_t launch_cg_tiled_range(const llb_ctx& c, const void* in, void* out, int zlo, int zhi, cudaStream_t st);
 
 // One box of a batched ensemble: its state copies for this step and its items.
 struct BatchDom {

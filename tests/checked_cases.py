@@ -178,6 +178,9 @@ def two_component():
                     tol = TOL[storage] if storage == llb.LLB_F64 else 1e-4
                     _case(f"d3q{q}-{sh}-cg-{SNAME[storage]}-v{v}",
                           lambda p=p: (_run(shape, q, TAU_2, m0, p), ref), tol)
+                    if v == 0:  # the host-to-host step launches the kernel on z-slabs
+                        _case(f"d3q{q}-{sh}-cg-step_host-{SNAME[storage]}",
+                              lambda p=p: (_run(shape, q, TAU_2, m0, p, host_step=True), ref), tol)
 
 
 def batches():

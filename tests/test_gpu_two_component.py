@@ -208,3 +208,65 @@ def test_smooth_normal_matches_oracle(q):
         got, _ = run_gpu(shape, q, tau, steps, rho=np.stack([r1, r2]), u=u, ncomp=2, storage=storage,
                          beta=0.7, A_s=0.02, A_h=0.0, grad_eps=0.02)
         assert_groups(got, ref, tol, GROUPS_2, what=f"D3Q{q} smooth storage {storage}")
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+@pytest.mark.parametrize("A_h", [0.01, 0.0], ids=["nci", "no-nci"])
+@pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("shape", [(40, 24, 64), (37, 11, 29), (12, 12, 12)], ids=lambda s: "x".join(map(str, s)))
+def test_step_host_matches_sequential(shape, storage, A_h, nsteps):
+    """llb_step_host for two components (slab copies overlapped with per-slab
+    steps; slabs at least as thick as the gradient and probe reach) gives bit
+    for bit what llb_init_moments + llb_step + llb_get_moments give."""
+    nx, ny, nz = shape
+    r = min(nx, ny, nz) / 4
+    r1, r2, u = inputs.droplets(nx, ny, nz, [(nx / 3, ny / 2, nz / 2), (2 * nx / 3, ny / 2 + 0.5, nz / 2 + 1)],
+                                [r, r], [(0.03, 0, 0.01), (-0.03, 0, -0.01)])
+    hdt = np.float32 if storage == llb.LLB_F32 else np.float64
+    h_in = np.ascontiguousarray(_moments(r1, r2, u).astype(hdt))
+    prm = tc.CGParams(beta=0.7, A_s=0.02, A_h=A_h, h_c=3, g_min=1e-8)
+    out = []
+    for piped in (False, True):
+        ctx = llb.llb_create(nx, ny, nz, 27, 0.9, llb.llb_params_default(**_params(prm, storage)))
+        try:
+            res = np.empty_like(h_in)
+            if piped:
+                llb.llb_step_host(ctx, h_in, res, nsteps)
+            else:
+                llb.llb_init_moments(ctx, h_in)
+                llb.llb_step(ctx, nsteps)
+                llb.llb_get_moments(ctx, res)
+            assert llb.llb_steps_done(ctx) == nsteps
+            again = llb.llb_get_moments(ctx, np.empty_like(h_in))
+        finally:
+            llb.llb_destroy(ctx)
+        assert np.array_equal(again, res)
+        out.append(res)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_init_accepts_small_negative_colour_density_and_rejects_bad_total():
+    """A stepped colour-gradient field can hold slightly negative colour
+    densities near interfaces; it must reload (canonical restart).  A total
+    density <= 0 or a non-finite value is refused with LLB_EUNSTABLE."""
+    n = 12
+    r1, r2, u = inputs.droplets(n, n, n, [(6.0, 6.0, 6.0)], [3.0], [(0.0, 0.0, 0.0)])
+    m = _moments(r1, r2, u)
+    m[1, 6, 6, 6] = -1e-6          # rho2 slightly negative inside the droplet
+    p = llb.llb_params_default(ncomp=2, storage=llb.LLB_F64)
+    ctx = llb.llb_create(n, n, n, 19, 0.9, p)
+    try:
+        llb.llb_init_moments(ctx, m)
+        llb.llb_step(ctx, 2)
+        bad = m.copy()
+        bad[0, 3, 3, 3] = -2.0      # rho1 + rho2 < 0
+        with pytest.raises(llb.LLBError) as e:
+            llb.llb_init_moments(ctx, bad)
+        assert e.value.status == llb.LLB_EUNSTABLE
+        nan = m.copy()
+        nan[1, 2, 2, 2] = np.nan
+        with pytest.raises(llb.LLBError) as e:
+            llb.llb_init_moments(ctx, nan)
+        assert e.value.status == llb.LLB_EUNSTABLE
+    finally:
+        llb.llb_destroy(ctx)
