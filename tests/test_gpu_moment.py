@@ -393,7 +393,8 @@ def test_autotune_keeps_state(q):
 
 
 @pytest.mark.parametrize("nsteps", [1, 3])
-@pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("storage", [llb.LLB_F32, llb.LLB_F64, llb.LLB_F16S, llb.LLB_BF16S],
+                         ids=["f32", "f64", "f16", "bf16"])
 @pytest.mark.parametrize("shape", [(64, 48, 40), (67, 45, 37), (33, 9, 5), (40, 24, 264)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_step_host_matches_sequential(shape, storage, nsteps):
@@ -401,7 +402,7 @@ def test_step_host_matches_sequential(shape, storage, nsteps):
     what llb_init_moments + llb_step + llb_get_moments give."""
     nx, ny, nz = shape
     m0 = inputs.random_moments(nx, ny, nz, seed=nx + ny + nz)
-    hdt = np.float32 if storage == llb.LLB_F32 else np.float64
+    hdt = np.float64 if storage == llb.LLB_F64 else np.float32
     h_in = np.ascontiguousarray(m0.astype(hdt))
     out = []
     for piped in (False, True):
