@@ -99,9 +99,9 @@ def build(verbose: bool = False, extra=None, force: bool = False, checked: bool 
 def build_all(verbose: bool = False, force: bool = False):
     """Both libraries, their translation units compiled by one pool."""
     n = 2 * len(sources())
-    with cf.ThreadPoolExecutor(max_workers=min(n, os.cpu_count() or 4)) as ex:
-        futs = [cf.ThreadPoolExecutor(max_workers=1).submit(build, verbose, None, force, chk, ex)
-                for chk in (False, True)]
+    with cf.ThreadPoolExecutor(max_workers=min(n, os.cpu_count() or 4)) as pool, \
+            cf.ThreadPoolExecutor(max_workers=2) as outer:
+        futs = [outer.submit(build, verbose, None, force, chk, pool) for chk in (False, True)]
         return [f.result() for f in futs]
 
 
