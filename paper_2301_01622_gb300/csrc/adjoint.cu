@@ -49,10 +49,12 @@ namespace {
 
 constexpr int kAdjThreads = 128;
 
+// The ten fields of node i of a one-component buffer (state or cotangent; the
+// field order of FieldMap).
 template <class T>
 __device__ __forceinline__ void load10(const T* __restrict__ p, size_t i, size_t fs, T* v) {
 #pragma unroll
-    for (int f = 0; f < 10; ++f) v[f] = p[f * fs + i];
+    for (int f = 0; f < 10; ++f) v[f] = p[FieldMap<T, 10>::at(i, f, fs)];
 }
 
 // Adjoint of one step at source node y (one thread per node).  lam_new, m and
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const T* __restric
         out[3] = lj[2] + om * rinv * (T(2) * jz * la[2] + jx * la[4] + jy * la[5]);
         for (int k = 0; k < 6; ++k) out[4 + k] = (T(1) - om) * la[k];
 #pragma unroll
-        for (int f = 0; f < 10; ++f) lam[f * lay.fs + i0] = out[f];
+        for (int f = 0; f < 10; ++f) lam[FieldMap<T, 10>::at(i0, f, lay.fs)] = out[f];
         // dL/domega: lam'_A : (j j / rho - A)
         for (int k = 0; k < 6; ++k) part += (double)la[k] * ((double)jj[k] * (double)rinv - (double)s[4 + k]);
     }
@@ -577,8 +579,8 @@ __global__ void k_cot_canon_to_shifted(const void* __restrict__ g, int dt, T* __
         const int x = (int)(i % L.nx);
         const size_t r = i / L.nx;
         const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
-        lam[j] = (T)(v[0] + kCs2 * (v[4] + v[5] + v[6]));
-        for (int f = 1; f < 10; ++f) lam[f * L.fs + j] = (T)v[f];
+        lam[FieldMap<T, 10>::at(j, 0, L.fs)] = (T)(v[0] + kCs2 * (v[4] + v[5] + v[6]));
+        for (int f = 1; f < 10; ++f) lam[FieldMap<T, 10>::at(j, f, L.fs)] = (T)v[f];
     }
 }
 
@@ -590,7 +592,7 @@ __global__ void k_cot_shifted_to_canon(const T* __restrict__ lam, void* __restri
         const size_t r = i / L.nx;
         const size_t j = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
         double v[10];
-        for (int f = 0; f < 10; ++f) v[f] = (double)lam[f * L.fs + j];
+        for (int f = 0; f < 10; ++f) v[f] = (double)lam[FieldMap<T, 10>::at(j, f, L.fs)];
         v[0] -= kCs2 * (v[4] + v[5] + v[6]);
         for (int f = 0; f < 10; ++f) {
             if (dt == LLB_F64) static_cast<double*>(g)[f * N + i] = v[f];

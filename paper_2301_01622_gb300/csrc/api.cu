@@ -4,6 +4,7 @@
 // host code only validates, allocates, copies and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,24 @@ int fields_of(const llb_ctx& c) {
 using namespace llb;
 
 namespace {
+
+// The moment-only state carries periodic ghosts (TMA tile boxes); its rows
+// are 32-aligned for the one-component FP32 state (fields interleaved per 32
+// nodes, FieldMap).  The population schemes keep dense populations and dense
+// moment temporaries.
+Layout layout_of(const llb_ctx& c) {
+    const bool moment = c.scheme == LLB_SCHEME_MOMENT;
+    const int align = (moment && c.ncomp == 1 && c.storage == LLB_F32) ? 32 : 8;
+    return make_layout(c.nx, c.ny, c.nz, moment, c.ncomp == 2 ? 2 : 1, align);
+}
+
+// Bytes of one state copy.  A population state also holds the shifted
+// moments of init and read-back (10 or 11 fields of stride lay.fs).
+size_t state_bytes_of(const llb_ctx& c) {
+    const size_t mom = (size_t)(c.ncomp == 2 ? 11 : 10) * c.lay.fs;
+    if (c.scheme == LLB_SCHEME_MOMENT) return (size_t)c.nf * c.lay.fs * c.elem;
+    return std::max((size_t)c.nf * c.N, mom) * c.elem;
+}
 
 int fail(llb_ctx* c, int code, const std::string& m) {
     if (c) {
@@ -106,11 +125,8 @@ int validate(int nx, int ny, int nz, int lattice, double tau, const llb_params& 
     c->N = (size_t)nx * ny * nz;
     c->nf = fields_of(*c);
     c->elem = elem_size(p.storage);
-    // the moment-only state carries periodic ghosts (TMA tile boxes); the
-    // population schemes keep dense populations and dense moment temporaries
-    c->lay = make_layout(nx, ny, nz, c->scheme == LLB_SCHEME_MOMENT, c->ncomp == 2 ? 2 : 1);
-    c->state_bytes = c->scheme == LLB_SCHEME_MOMENT ? (size_t)c->nf * c->lay.fs * c->elem
-                                                    : (size_t)c->nf * c->N * c->elem;
+    c->lay = layout_of(*c);
+    c->state_bytes = state_bytes_of(*c);
     return LLB_OK;
 }
 
@@ -258,12 +274,11 @@ int llb_footprint_query(int nx, int ny, int nz, int lattice, const llb_params* p
     if (ncomp != 1 && ncomp != 2) return LLB_EINVAL;
     c.ncomp = ncomp;
     c.nf = fields_of(c);
-    if (ncomp == 2 && c.scheme == LLB_SCHEME_MOMENT) c.lay = make_layout(nx, ny, nz, true, 2);
+    c.lay = layout_of(c);
     out->fields = c.nf;
     out->arrays = 2 * c.nf;
     out->bytes_per_node = 2 * (size_t)c.nf * c.elem;
-    out->state_bytes = c.scheme == LLB_SCHEME_MOMENT ? (size_t)c.nf * c.lay.fs * c.elem
-                                                     : (size_t)c.nf * c.N * c.elem;
+    out->state_bytes = state_bytes_of(c);
     out->stream_bytes_per_node = 2 * (size_t)c.nf * c.elem;
     return LLB_OK;
 }

@@ -50,7 +50,7 @@ __device__ __forceinline__ void put(T* __restrict__ st, const Layout& L, int x, 
     for_node_and_ghosts(L, x, y, [&](int gx, int gy) {
         const size_t j = L.at(gx, gy, z);
 #pragma unroll
-        for (int f = 0; f < 10; ++f) st[f * L.fs + j] = to_store<T>(v[f], f);
+        for (int f = 0; f < 10; ++f) st[FieldMap<T, 10>::at(j, f, L.fs)] = to_store<T>(v[f], f);
     });
 }
 
@@ -84,11 +84,12 @@ __global__ void k_shifted_to_canon(const T* __restrict__ st, void* __restrict__ 
         int x, y, z;
         decode(L, i, x, y, z);
         const size_t j = L.at(x, y, z);
-        const double rho = 1.0 + rd_field(st[j], 0);
+        using FM = FieldMap<T, 10>;
+        const double rho = 1.0 + rd_field(st[FM::at(j, 0, L.fs)], 0);
         wrt(canon, i, cdt, rho);
-        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f));
-        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f) + kCs2 * rho);
-        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, rd_field(st[f * L.fs + j], f));
+        for (int f = 1; f < 4; ++f) wrt(canon, f * N + i, cdt, rd_field(st[FM::at(j, f, L.fs)], f));
+        for (int f = 4; f < 7; ++f) wrt(canon, f * N + i, cdt, rd_field(st[FM::at(j, f, L.fs)], f) + kCs2 * rho);
+        for (int f = 7; f < 10; ++f) wrt(canon, f * N + i, cdt, rd_field(st[FM::at(j, f, L.fs)], f));
     }
 }
 

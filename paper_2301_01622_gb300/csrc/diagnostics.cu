@@ -85,11 +85,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
         const int x = (int)(n % L.nx);
         const size_t r = n / L.nx;
         const size_t i = L.at(x, (int)(r % L.ny), (int)(r / L.ny));
-        const double d = rd_field(m[o * F + i], 0);
-        const double jx = rd_field(m[(o + 1) * F + i], 1), jy = rd_field(m[(o + 2) * F + i], 2),
-                     jz = rd_field(m[(o + 3) * F + i], 3);
+        using FM = FieldMap<T, NC == 2 ? 11 : 10>;
+        const double d = rd_field(m[FM::at(i, o, F)], 0);
+        const double jx = rd_field(m[FM::at(i, o + 1, F)], 1), jy = rd_field(m[FM::at(i, o + 2, F)], 2),
+                     jz = rd_field(m[FM::at(i, o + 3, F)], 3);
         const double rho = 1.0 + d;
-        const double drop = NC == 2 ? rd_field(m[i], 0) : rho;
+        const double drop = NC == 2 ? rd_field(m[FM::at(i, 0, F)], 0) : rho;
         p.v[0] += d;
         p.v[1] += jx;
         p.v[2] += jy;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const T* __restri
         if (NC == 2) p.v[8] += drop;
         bool finite = isfinite(d) && isfinite(jx) && isfinite(jy) && isfinite(jz) && isfinite(drop);
 #pragma unroll
-        for (int f = o + 4; f < o + 10; ++f) finite = finite && isfinite(rd_field(m[f * F + i], f - o));
+        for (int f = o + 4; f < o + 10; ++f) finite = finite && isfinite(rd_field(m[FM::at(i, f, F)], f - o));
         if (!finite) p.v[7] = 1.0;
     }
     p = block_reduce(p);

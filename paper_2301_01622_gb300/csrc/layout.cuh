@@ -18,9 +18,20 @@
 // of ghosts are written for the same reason.  With them the tile plus halo a
 // CTA needs is one rectangular box with a 16-byte aligned x start, so one
 // TMA load fetches it without wrapping.
+//
+// Field order inside a buffer (FieldMap): field-major, f * fs + i, for every
+// state except the one-component FP32 state, which interleaves its ten
+// fields per block of 32 consecutive node indices: field f of node i sits at
+// (i & ~31) * 10 + 32 f + (i & 31).  A thread then reaches every field of
+// its node at a constant offset from one address, and the ten fields of a
+// warp's 32 nodes are one contiguous 1280-byte run.  That state's row pitch
+// is a multiple of 32 (blocks never straddle rows).  Every field stride fs is
+// a multiple of 32, so the last block of an interleaved buffer stays inside
+// NF * fs elements.
 #pragma once
 
 #include <cstddef>
+#include <type_traits>
 
 namespace llb {
 
@@ -38,12 +49,26 @@ struct Layout {
 
 constexpr int kGhostX = 8;  // ghost columns per side (one FP32 sector)
 
-inline Layout make_layout(int nx, int ny, int nz, bool padded, int ghost_rows = 1) {
+// Element offset of field f of node i in a buffer of NF fields of type S.
+template <class S, int NF>
+struct FieldMap {
+    static constexpr bool kInterleaved = std::is_same<S, float>::value && NF == 10;
+    __host__ __device__ __forceinline__ static size_t at(size_t i, int f, size_t fs) {
+        if constexpr (kInterleaved)
+            return (i & ~size_t(31)) * NF + (size_t)f * 32 + (i & 31);
+        else
+            return (size_t)f * fs + i;
+    }
+};
+
+// row_align: multiple the padded row pitch is rounded up to (8; 32 for the
+// interleaved one-component FP32 state).
+inline Layout make_layout(int nx, int ny, int nz, bool padded, int ghost_rows = 1, int row_align = 8) {
     Layout L;
     L.nx = nx; L.ny = ny; L.nz = nz;
     if (padded) {
         L.xo = kGhostX; L.yo = ghost_rows;
-        L.px = ((nx + 2 * kGhostX + 7) / 8) * 8;
+        L.px = ((nx + 2 * kGhostX + row_align - 1) / row_align) * row_align;
         L.py = ny + 2 * ghost_rows;
         L.ghosts = 1;
     } else {
@@ -51,7 +76,7 @@ inline Layout make_layout(int nx, int ny, int nz, bool padded, int ghost_rows = 
         L.px = nx; L.py = ny;
         L.ghosts = 0;
     }
-    L.fs = (size_t)L.px * L.py * nz;
+    L.fs = ((size_t)L.px * L.py * nz + 31) / 32 * 32;
     return L;
 }
 

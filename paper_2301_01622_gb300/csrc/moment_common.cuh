@@ -29,19 +29,21 @@ namespace mom {
 constexpr long long kDrainBudget = 100000000LL;
 
 // Ten shifted moments of node idx from a state of element type S (converted to T).
+// Ten shifted moments of node idx (index of the node in the state buffer p).
 template <class T, class S>
 __device__ __forceinline__ Mom<T> load_mom(const S* __restrict__ p, size_t idx, size_t fs) {
+    using FM = FieldMap<S, 10>;
     Mom<T> m;
-    m.d = ld_field<T>(p + idx, 0);
-    m.jx = ld_field<T>(p + fs + idx, 1);
-    m.jy = ld_field<T>(p + 2 * fs + idx, 2);
-    m.jz = ld_field<T>(p + 3 * fs + idx, 3);
-    m.axx = ld_field<T>(p + 4 * fs + idx, 4);
-    m.ayy = ld_field<T>(p + 5 * fs + idx, 5);
-    m.azz = ld_field<T>(p + 6 * fs + idx, 6);
-    m.axy = ld_field<T>(p + 7 * fs + idx, 7);
-    m.axz = ld_field<T>(p + 8 * fs + idx, 8);
-    m.ayz = ld_field<T>(p + 9 * fs + idx, 9);
+    m.d = ld_field<T>(p + FM::at(idx, 0, fs), 0);
+    m.jx = ld_field<T>(p + FM::at(idx, 1, fs), 1);
+    m.jy = ld_field<T>(p + FM::at(idx, 2, fs), 2);
+    m.jz = ld_field<T>(p + FM::at(idx, 3, fs), 3);
+    m.axx = ld_field<T>(p + FM::at(idx, 4, fs), 4);
+    m.ayy = ld_field<T>(p + FM::at(idx, 5, fs), 5);
+    m.azz = ld_field<T>(p + FM::at(idx, 6, fs), 6);
+    m.axy = ld_field<T>(p + FM::at(idx, 7, fs), 7);
+    m.axz = ld_field<T>(p + FM::at(idx, 8, fs), 8);
+    m.ayz = ld_field<T>(p + FM::at(idx, 9, fs), 9);
     return m;
 }
 
@@ -58,7 +60,7 @@ template <class S>
 __device__ __forceinline__ RawMom<S> load_raw(const S* __restrict__ p, size_t idx, size_t fs) {
     RawMom<S> r;
 #pragma unroll
-    for (int f = 0; f < 10; ++f) r.v[f] = __ldg(p + f * fs + idx);
+    for (int f = 0; f < 10; ++f) r.v[f] = __ldg(p + FieldMap<S, 10>::at(idx, f, fs));
     return r;
 }
 
@@ -80,16 +82,17 @@ __device__ __forceinline__ Mom<T> from_raw(const RawMom<S>& r) {
 
 template <class T, class S>
 __device__ __forceinline__ void store_mom(S* __restrict__ p, size_t idx, size_t fs, const Mom<T>& m) {
-    p[idx] = to_store<S>(m.d, 0);
-    p[fs + idx] = to_store<S>(m.jx, 1);
-    p[2 * fs + idx] = to_store<S>(m.jy, 2);
-    p[3 * fs + idx] = to_store<S>(m.jz, 3);
-    p[4 * fs + idx] = to_store<S>(m.axx, 4);
-    p[5 * fs + idx] = to_store<S>(m.ayy, 5);
-    p[6 * fs + idx] = to_store<S>(m.azz, 6);
-    p[7 * fs + idx] = to_store<S>(m.axy, 7);
-    p[8 * fs + idx] = to_store<S>(m.axz, 8);
-    p[9 * fs + idx] = to_store<S>(m.ayz, 9);
+    using FM = FieldMap<S, 10>;
+    p[FM::at(idx, 0, fs)] = to_store<S>(m.d, 0);
+    p[FM::at(idx, 1, fs)] = to_store<S>(m.jx, 1);
+    p[FM::at(idx, 2, fs)] = to_store<S>(m.jy, 2);
+    p[FM::at(idx, 3, fs)] = to_store<S>(m.jz, 3);
+    p[FM::at(idx, 4, fs)] = to_store<S>(m.axx, 4);
+    p[FM::at(idx, 5, fs)] = to_store<S>(m.ayy, 5);
+    p[FM::at(idx, 6, fs)] = to_store<S>(m.azz, 6);
+    p[FM::at(idx, 7, fs)] = to_store<S>(m.axy, 7);
+    p[FM::at(idx, 8, fs)] = to_store<S>(m.axz, 8);
+    p[FM::at(idx, 9, fs)] = to_store<S>(m.ayz, 9);
 }
 
 // Store node (x, y, z) and its periodic ghost copies.

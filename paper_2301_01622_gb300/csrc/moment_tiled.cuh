@@ -61,6 +61,27 @@ struct Tiled {
 template <class S>
 constexpr int pf_pad() { return 16 / (int)sizeof(S) > 4 ? 16 / (int)sizeof(S) : 4; }
 
+// Moments of a node of plane offset zoff: field-major storage addresses them
+// from the node's own pointer p (kept per work item); the interleaved FP32
+// state needs the node's absolute index o + zoff (its field offsets depend on
+// it).  Likewise for the store of an output node at q (absolute index q - out).
+template <class S>
+__device__ __forceinline__ RawMom<S> load_node_raw(const S* __restrict__ in, const S* __restrict__ p, long long o,
+                                                   size_t zoff, size_t fs) {
+    if constexpr (FieldMap<S, 10>::kInterleaved)
+        return load_raw(in, (size_t)o + zoff, fs);
+    else
+        return load_raw(p + zoff, 0, fs);
+}
+
+template <class T, class S>
+__device__ __forceinline__ void store_node_mom(S* __restrict__ out, S* __restrict__ q, size_t fs, const Mom<T>& m) {
+    if constexpr (FieldMap<S, 10>::kInterleaved)
+        store_mom(out, (size_t)(q - out), fs, m);
+    else
+        store_mom(q, 0, fs, m);
+}
+
 template <class L, class T, int BX, int BY, int MINB, int OPT, int PD, class S>
 __global__ void __launch_bounds__(BX * BY, MINB)
     k_moment_tiled(const S* __restrict__ in, S* __restrict__ out, Layout lay, T omega, Sched sc, int zlo, int nzr,
@@ -137,15 +158,15 @@ __global__ void __launch_bounds__(BX * BY, MINB)
         size_t zn_off = (size_t)zn * plane;
         const long long o1 = in1 - in, o2 = in2 - in;  // node offsets within a field (plane 0)
         RawMom<S> m1{}, m2{};  // converted at the collision
-        if (LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_raw(in1 + zn_off, 0, lay.fs);
-        if (has2 && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_raw(in2 + zn_off, 0, lay.fs);
+        if (LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_node_raw(in, in1, o1, zn_off, lay.fs);
+        if (has2 && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_node_raw(in, in2, o2, zn_off, lay.fs);
 
         Acc<T> a0, a1, a2;
         a0.zero(); a1.zero(); a2.zero();
 
         auto put = [&](const Acc<T>& A, int z) {
             const Mom<T> r = A.finish();
-            if (LLB_IN(out1 - out, lay.fs, kChkStore)) store_mom(out1, 0, lay.fs, r);
+            if (LLB_IN(out1 - out, lay.fs, kChkStore)) store_node_mom(out, out1, lay.fs, r);
             if (ghost) store_node(out, lay, ox, oy, z, r);
             out1 += plane;
         };
@@ -170,13 +191,13 @@ __global__ void __launch_bounds__(BX * BY, MINB)
                 }
             }
             const Mom<T> c1 = collide<T, FAST>(from_raw<T>(m1), omega);
-            if (more && LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_raw(in1 + zn_off, 0, lay.fs);
+            if (more && LLB_IN(o1 + (long long)zn_off, lay.fs, kChkLoad)) m1 = load_node_raw(in, in1, o1, zn_off, lay.fs);
             publish<L, T, HN>(G, n1, c1);
             T g_m, g_0, g_p;
             own_column<L, T>(c1, g_m, g_0, g_p);
             if (has2) {
                 const Mom<T> c2 = collide<T, FAST>(from_raw<T>(m2), omega);
-                if (more && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_raw(in2 + zn_off, 0, lay.fs);
+                if (more && LLB_IN(o2 + (long long)zn_off, lay.fs, kChkLoad)) m2 = load_node_raw(in, in2, o2, zn_off, lay.fs);
                 publish_halo<L, T, HN>(G, n2, role2, sx2, c2);
             }
             if constexpr (SPLIT) {

@@ -29,7 +29,11 @@ struct TmaCfg {
     static constexpr int NT = BX * BY;
     static constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY, NH = 2 * BX + 2 * BY + 4;
     static constexpr int NS = n_xy_shifted<L>();
-    static constexpr int SW = BX + 8;        // staged row: x0-4 .. x0+BX+3
+    // the interleaved FP32 state (FieldMap) is staged in whole 32-node blocks:
+    // NB blocks cover the padded columns x0+7 .. x0+BX+8 of the tile and halo
+    static constexpr bool IL = FieldMap<T, 10>::kInterleaved;
+    static constexpr int NB = BX / 32 + 1;
+    static constexpr int SW = IL ? 32 * NB : BX + 8;  // staged row: blocks, or x0-4 .. x0+BX+3
     static constexpr int SR = BY + 2;        // staged rows: y0-1 .. y0+BY
     static constexpr int SF = SW * SR;       // elements per staged field
     static constexpr int STAGE_BYTES = 10 * SF * (int)sizeof(T);
@@ -42,24 +46,48 @@ struct TmaCfg {
     static_assert(NH <= NT, "halo must fit one node per thread");
     static_assert(SW * (int)sizeof(T) % 16 == 0, "TMA box row must be a multiple of 16 bytes");
     static_assert(SW <= 256 && SR <= 256, "TMA box dimension limit");
+    static_assert(!IL || BX % 32 == 0, "interleaved boxes need tiles of whole 32-node blocks");
 };
 
-template <class T, int SF, int SW>
+// Moments of staged node (hx, hy) of the tile plus halo.  Field-major stage:
+// [field][row][x0-4 ..]; interleaved stage: [row][block][field][lane], node
+// hx at padded column x0+7+hx.
+template <class T, class C>
 __device__ __forceinline__ Mom<T> stage_mom(const T* __restrict__ S, int hx, int hy) {
+    constexpr int SF = C::SF, SW = C::SW;
     Mom<T> m{};
-    if (!LLB_IN(hy * SW + hx + 3, SF, kChkStage)) return m;
-    const T* p = S + hy * SW + hx + 3;
+    int o, fstep;
+    if constexpr (C::IL) {
+        const int rel = 7 + hx;
+        o = ((hy * C::NB + (rel >> 5)) * 10) * 32 + (rel & 31);
+        fstep = 32;
+    } else {
+        o = hy * SW + hx + 3;
+        fstep = SF;
+    }
+    if (!LLB_IN(o + 9 * fstep, 10 * SF, kChkStage)) return m;
+    const T* p = S + o;
     m.d = p[0];
-    m.jx = p[SF];
-    m.jy = p[2 * SF];
-    m.jz = p[3 * SF];
-    m.axx = p[4 * SF];
-    m.ayy = p[5 * SF];
-    m.azz = p[6 * SF];
-    m.axy = p[7 * SF];
-    m.axz = p[8 * SF];
-    m.ayz = p[9 * SF];
+    m.jx = p[fstep];
+    m.jy = p[2 * fstep];
+    m.jz = p[3 * fstep];
+    m.axx = p[4 * fstep];
+    m.ayy = p[5 * fstep];
+    m.azz = p[6 * fstep];
+    m.axy = p[7 * fstep];
+    m.axz = p[8 * fstep];
+    m.ayz = p[9 * fstep];
     return m;
+}
+
+// One stage load: the tile-plus-halo box of plane z.
+template <class C>
+__device__ __forceinline__ void stage_load(uint32_t dst, const CUtensorMap* map, const Layout& lay, int x0, int y0, int z,
+                                           uint32_t bar) {
+    if constexpr (C::IL)
+        tma_load_5d(dst, map, 0, 0, (x0 + lay.xo - 1) / 32, y0 + lay.yo - 1, z, bar);
+    else
+        tma_load_4d(dst, map, x0 + lay.xo - 4, y0 + lay.yo - 1, z, 0, bar);
 }
 
 template <class L, class T, class C>
@@ -67,7 +95,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     k_moment_tma(const __grid_constant__ CUtensorMap tmap, T* __restrict__ out, Layout lay, T omega, Sched sc,
                  int* __restrict__ err, long long wait_budget, int extra_tx) {
     constexpr int BX = C::BX, BY = C::BY, NST = C::NST, HX = C::HX, HN = C::HN, NS = C::NS;
-    constexpr int SF = C::SF, SW = C::SW;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     T* const Gbase = reinterpret_cast<T*>(smem + C::G_OFF);
@@ -95,8 +122,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     int buf = 0;
     unsigned q = 0;         // sequence number of the next source plane (all items)
     unsigned issued = 0;    // sequence numbers < issued have a TMA in flight or done (thread 0)
-    // box origin: real (x0 - 4, y0 - 1) in padded coordinates
-    const int bxo = lay.xo - 4, byo = lay.yo - 1;
 
     for (int it = blockIdx.x; it < sc.nitems; it += gridDim.x) {
         int x0, y0, za, zb;  // outputs za .. zb-1 of the tile at (x0, y0)
@@ -110,8 +135,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 const unsigned qq = q0 + i;
                 const uint32_t bar = bar0 + 8 * (qq % NST);
                 mbar_arrive_expect_tx(bar, C::STAGE_BYTES + extra_tx);
-                tma_load_4d(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(za - 1 + i, nz), 0,
-                            bar);
+                stage_load<C>(stage0 + (qq % NST) * C::STAGE_STRIDE, &tmap, lay, x0, y0, pmod(za - 1 + i, nz), bar);
             }
             issued = q0 + min(NST, P);
         }
@@ -131,12 +155,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             T* const G = Gbase + buf * (NS * HN);
             T g_m = T(0), g_0 = T(0), g_p = T(0);
             if (ok) {
-                const Mom<T> c1 = collide<T, true>(stage_mom<T, SF, SW>(S, tx + 1, ty + 1), omega);
+                const Mom<T> c1 = collide<T, true>(stage_mom<T, C>(S, tx + 1, ty + 1), omega);
                 publish<L, T, HN>(G, n1, c1);
                 own_column<L, T>(c1, g_m, g_0, g_p);
                 if (has2)
                     publish_halo<L, T, HN>(G, n2, role2, sx2,
-                                           collide<T, true>(stage_mom<T, SF, SW>(S, hx2, hy2), omega));
+                                           collide<T, true>(stage_mom<T, C>(S, hx2, hy2), omega));
             }
             if (__syncthreads_or(!ok)) return false;
             // every thread is done with stage k: refill it with plane s + NST
@@ -145,13 +169,18 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                 const unsigned qq = q + NST;
                 const uint32_t bar = bar0 + 8 * k;
                 mbar_arrive_expect_tx(bar, C::STAGE_BYTES + extra_tx);
-                tma_load_4d(stage0 + k * C::STAGE_STRIDE, &tmap, x0 + bxo, y0 + byo, pmod(s + NST, nz), 0, bar);
+                stage_load<C>(stage0 + k * C::STAGE_STRIDE, &tmap, lay, x0, y0, pmod(s + NST, nz), bar);
                 issued = qq + 1;
             }
             gather<L, T, HN, HX>(G, n1, g_m, g_0, g_p, X, Y, Z);
             if (s - 1 >= za && store_ok) {
                 const Mom<T> r = X.finish();
-                if (LLB_IN(out1 - out, lay.fs, kChkStore)) store_mom(out1, 0, lay.fs, r);
+                if (LLB_IN(out1 - out, lay.fs, kChkStore)) {
+                    if constexpr (C::IL)
+                        store_mom(out, (size_t)(out1 - out), lay.fs, r);  // absolute index (interleaved)
+                    else
+                        store_mom(out1, 0, lay.fs, r);
+                }
                 if (ghost) store_node(out, lay, ox, oy, s - 1, r);
                 out1 += plane;
             }
@@ -266,6 +295,19 @@ bool encode_box_map(const llb_ctx& c, void* buf, int box_w, int box_h, CUtensorM
         default: return false;
     }
     const size_t es = elem_size(c.storage);
+    if (c.storage == LLB_F32) {
+        // interleaved state (FieldMap): dims (lane, field, 32-node block, y, z);
+        // a box of box_w / 32 whole blocks, all ten fields
+        if (box_w % 32 != 0 || Lo.px % 32 != 0) return false;
+        const cuuint64_t dims[5] = {32, 10, (cuuint64_t)Lo.px / 32, (cuuint64_t)Lo.py, (cuuint64_t)Lo.nz};
+        const cuuint64_t strides[4] = {32 * es, 320 * es, (cuuint64_t)Lo.px * 10 * es,
+                                       (cuuint64_t)Lo.px * Lo.py * 10 * es};
+        const cuuint32_t box[5] = {32, 10, (cuuint32_t)box_w / 32, (cuuint32_t)box_h, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        return encode(out, dt, 5, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     if ((size_t)box_w * es % 16 != 0) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)Lo.px, (cuuint64_t)Lo.py, (cuuint64_t)Lo.nz, 10};
     const cuuint64_t strides[3] = {(cuuint64_t)Lo.px * es, (cuuint64_t)Lo.px * Lo.py * es, (cuuint64_t)Lo.fs * es};

@@ -34,20 +34,27 @@
 namespace llb {
 namespace {
 
-template <class T>
+// Ten shifted moments of node idx in a moment buffer of NF fields (10: the
+// one-component state, whose field order follows FieldMap; 11: the
+// two-component state, field-major, read from its field 1 on).
+template <int NF, class T>
 __device__ __forceinline__ Mom<T> load_mom(const T* __restrict__ p, size_t idx, size_t N) {
+    using FM = FieldMap<T, NF>;
     Mom<T> m;
-    m.d = p[idx]; m.jx = p[N + idx]; m.jy = p[2 * N + idx]; m.jz = p[3 * N + idx];
-    m.axx = p[4 * N + idx]; m.ayy = p[5 * N + idx]; m.azz = p[6 * N + idx];
-    m.axy = p[7 * N + idx]; m.axz = p[8 * N + idx]; m.ayz = p[9 * N + idx];
+    m.d = p[FM::at(idx, 0, N)]; m.jx = p[FM::at(idx, 1, N)]; m.jy = p[FM::at(idx, 2, N)];
+    m.jz = p[FM::at(idx, 3, N)]; m.axx = p[FM::at(idx, 4, N)]; m.ayy = p[FM::at(idx, 5, N)];
+    m.azz = p[FM::at(idx, 6, N)]; m.axy = p[FM::at(idx, 7, N)]; m.axz = p[FM::at(idx, 8, N)];
+    m.ayz = p[FM::at(idx, 9, N)];
     return m;
 }
 
-template <class T>
+template <int NF, class T>
 __device__ __forceinline__ void store_mom(T* __restrict__ p, size_t idx, size_t N, const Mom<T>& m) {
-    p[idx] = m.d; p[N + idx] = m.jx; p[2 * N + idx] = m.jy; p[3 * N + idx] = m.jz;
-    p[4 * N + idx] = m.axx; p[5 * N + idx] = m.ayy; p[6 * N + idx] = m.azz;
-    p[7 * N + idx] = m.axy; p[8 * N + idx] = m.axz; p[9 * N + idx] = m.ayz;
+    using FM = FieldMap<T, NF>;
+    p[FM::at(idx, 0, N)] = m.d; p[FM::at(idx, 1, N)] = m.jx; p[FM::at(idx, 2, N)] = m.jy;
+    p[FM::at(idx, 3, N)] = m.jz; p[FM::at(idx, 4, N)] = m.axx; p[FM::at(idx, 5, N)] = m.ayy;
+    p[FM::at(idx, 6, N)] = m.azz; p[FM::at(idx, 7, N)] = m.axy; p[FM::at(idx, 8, N)] = m.axz;
+    p[FM::at(idx, 9, N)] = m.ayz;
 }
 
 template <class L, class T, bool BGK>
@@ -108,7 +115,7 @@ __global__ void k_pop_from_moments(const T* __restrict__ mom, T* __restrict__ st
             for (int cx = -1; cx <= 1; ++cx) {
                 if (!L::has(cx, cy, cz)) continue;
                 const size_t s = LLB_CLAMP(lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz)), lay.fs, kChkLoad);
-                const Mom<T> m = load_mom(mom, s, lay.fs);
+                const Mom<T> m = load_mom<10>(mom, s, lay.fs);
                 st[(size_t)k * N + idx] = g_dir<L, T>(m, g_shared(m), cx, cy, cz);
                 ++k;
             }
@@ -134,7 +141,7 @@ __global__ void k_moments_from_pop(const T* __restrict__ st, T* __restrict__ mom
                 acc.add(st[(size_t)k * N + s], cx, cy, cz);
                 ++k;
             }
-    store_mom(mom, LLB_CLAMP(lay.at(x, y, z), lay.fs, kChkStore), lay.fs, acc.finish());
+    store_mom<10>(mom, LLB_CLAMP(lay.at(x, y, z), lay.fs, kChkStore), lay.fs, acc.finish());
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +262,7 @@ __global__ void k_pop2_from_moments(const T* __restrict__ mom, T* __restrict__ s
                 if (!L::has(cx, cy, cz)) continue;
                 const size_t s = LLB_CLAMP(lay.at(wrap_idx(x + cx, nx), wrap_idx(y + cy, ny), wrap_idx(z + cz, nz)), lay.fs, kChkLoad);
                 const T r1 = mom[s];
-                const Mom<T> m = load_mom(mom + lay.fs, s, lay.fs);
+                const Mom<T> m = load_mom<11>(mom + lay.fs, s, lay.fs);
                 const T gr = g_dir<L, T>(m, g_shared(m), cx, cy, cz);
                 st[(size_t)k * N + idx] = gr;
                 st[(size_t)(L::Q + k) * N + idx] = r1 / (T(1) + m.d) * (T(L::w(cx, cy, cz)) + gr);
@@ -287,7 +294,7 @@ __global__ void k_moments2_from_pop(const T* __restrict__ st, T* __restrict__ mo
             }
     const size_t i = LLB_CLAMP(lay.at(x, y, z), lay.fs, kChkStore);
     mom[i] = r1;
-    store_mom(mom + lay.fs, i, lay.fs, acc.finish());
+    store_mom<11>(mom + lay.fs, i, lay.fs, acc.finish());
 }
 
 dim3 node_grid(const llb_ctx& c) { return dim3((c.nx + 127) / 128, c.ny, c.nz); }

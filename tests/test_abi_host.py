@@ -60,14 +60,17 @@ def test_storage_accounting_matches_paper():
     assert mom2.fields * 18 * 4 == g["stream_read_bytes_fp32_two_component_d3q19"]["value"]
     # bytes per node and state size (FP32)
     assert mom1.bytes_per_node == 80 and pop1.bytes_per_node == 152
-    # one state copy: 10 FP32 fields per node plus periodic ghost rows/columns
-    assert 10 * 4 * 128 ** 3 <= mom1.state_bytes <= 10 * 4 * 144 * 130 * 128
+    # one state copy: 10 FP32 fields per node plus periodic ghost rows/columns; the
+    # one-component FP32 state rounds its rows up to whole 32-node blocks
+    assert 10 * 4 * 128 ** 3 <= mom1.state_bytes == 10 * 4 * 160 * 130 * 128
     assert pop1.state_bytes == 19 * 4 * 128 ** 3
     q27 = llb.llb_footprint_query(8, 8, 8, 27, llb.llb_params_default(scheme=llb.LLB_SCHEME_POPULATION))
     assert q27.bytes_per_node == 216
     f64 = llb.llb_footprint_query(8, 8, 8, 27, llb.llb_params_default(storage=llb.LLB_F64))
     assert f64.bytes_per_node == 160
-    assert llb.llb_state_bytes(8, 8, 8, 19) == 10 * 4 * 24 * 10 * 8
+    assert llb.llb_state_bytes(8, 8, 8, 19) == 10 * 4 * 32 * 10 * 8
+    # other states keep rows rounded to 8 nodes (FP64: 8 + 16 ghost columns)
+    assert llb.llb_state_bytes(8, 8, 8, 19, llb.llb_params_default(storage=llb.LLB_F64)) == 10 * 8 * 24 * 10 * 8
 
 
 @pytest.mark.parametrize("args", [
