@@ -294,7 +294,9 @@ LLB_API int llb_steps_done(const llb_ctx* ctx, long long* out);
 /* Device pointer of the current state copy, its element type and the kernel
  * the context runs (for profiling and zero-copy views).  Bit-for-bit
  * checkpoint: the current state copy (llb_state_bytes bytes: the shifted
- * moments in the context's padded layout, ghost copies included), saved and
+ * moments in the context's padded layout, ghost copies included; field-major,
+ * except the one-component FP32 state, which interleaves its ten fields per
+ * block of 32 node positions), saved and
  * later written into the current state copy of a context created with the
  * same sizes and parameters (after its llb_init_*), resumes the run bit for
  * bit; llb_steps_done then counts from that restart. */
